@@ -1,0 +1,343 @@
+"""Benchmark of the Yee + UPML FDTD hot path on GB300 (one JSON line).
+
+Default workload: the large multilayer board (880 x 680 x 100 cells, four
+power/ground pairs, 12-cell UPML, 4 sources, 64 probes, running DFT to
+10 GHz over a 50000-step solve), FP32.  A bench "step" is a window of
+``--window`` leapfrog steps of that solve, each doing the whole hot path
+(UPML/boundary H, fused interior H+E, UPML/boundary E, sources, probes, and
+the FP64 running-DFT update at the end of the window).  The fields (3 GB in
+FP32) are far larger than L2, so no flush is needed between steps.
+
+value  = cell-updates / s (Gcell-updates/s) with inputs resident in HBM.
+e2e    = the same metric through the C-ABI with host buffers: every step
+         re-uploads the material volume (fdtd_set_materials, host -> device),
+         runs the window and copies the spectra back (device -> host).
+roofline: the fused interior kernel (the dominant one), algorithmic bytes per
+         interior node-update (49 B in FP32: 6 fields read + written, 1 id
+         byte; 25 B with 16-bit storage) over its mean launch time measured
+         with CUDA events on its stream, against the measured HBM copy
+         bandwidth.
+cpu_baseline: the FP64 oracle on the same full-size grid for a few steps.
+
+Other workloads: --workload small | realistic | batched | served.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Yee+UPML Gcell-updates/s & % HBM roofline; batched/served solves/s, p50/p99 latency"
+
+
+def _measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def _workload(name: str, seed_offset: int = 0):
+    from paper_1008_2602_gb300 import workloads as W
+    if name == "small":
+        return W.small_pcb(seed=1 + seed_offset)
+    if name == "realistic":
+        return W.realistic_board(seed=2 + seed_offset)
+    if name == "multilayer":
+        return W.multilayer_board(seed=3 + seed_offset)
+    if name == "multilayer_q":
+        return W.multilayer_board(seed=3 + seed_offset, scale=4)
+    raise ValueError(name)
+
+
+def _describe(prob, name, window, prec):
+    return {"workload": f"{prob.name} ({name}): {prob.nx}x{prob.ny}x{prob.nz} cells, "
+                        f"{len(prob.sources)} sources, {len(prob.probes)} probes, UPML {prob.upml_depth[0]} cells, "
+                        f"{prob.n_steps}-step solve, step = {window} leapfrog steps",
+            "cells": prob.cells, "leapfrog_steps_per_step": window, "precision": prec,
+            "l2": "inputs larger than L2 (no flush)" if prob.cells * 48 > 129e6 else
+                  "working set fits in L2 (not flushed)"}
+
+
+def _traffic_for(kernel_tag: str, nodes: int):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it
+    was taken on the current kernel source (scaled to `nodes`)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)[kernel_tag]
+        src = os.path.join(ROOT, "paper_1008_2602_gb300", "csrc", "fdtd_kernels.cu")
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        if d.get("kernel_sha") != sha:
+            return None
+        return d["bytes_per_node"] * nodes
+    except Exception:
+        return None
+
+
+def run_single(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_1008_2602_gb300 import solver
+
+    dev = local
+    torch.cuda.set_device(dev)
+    prob = _workload(args.workload, seed_offset=rank)
+    window = args.window
+    s = solver.Solver(prob, precision=args.precision)
+    inf = s.info()
+    cells = prob.cells
+    interior_nodes = inf["interior_nodes"]
+    stream = None
+
+    # warm-up
+    for _ in range(args.warmup):
+        s.step_profiled(window)
+    s.sync()
+
+    if world > 1:
+        torch.distributed.barrier()
+    phase = np.zeros(5)
+    with ClockSampler(dev) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            phase += s.step_profiled(window)
+        s.sync()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+    elapsed = t1 - t0
+    if world > 1:
+        t = torch.tensor([elapsed], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(t.item())
+    dev_ms = float(phase.sum())
+    total_updates = float(cells) * window * args.steps * world
+    value = total_updates / elapsed / 1e9
+
+    # roofline of the fused interior kernel: 12 field values + 1 id byte per
+    # node, plus 4 FP32 auxiliaries read and written on z-UPML nodes
+    es = 4 if args.precision == "fp32" else 2
+    bytes_per_node = 12 * es + (2 if inf["n_combo"] > 256 else 1)
+    upml_nodes = inf["fused_upml_nodes"]
+    alg_bytes = bytes_per_node * interior_nodes + 32 * upml_nodes
+    n_launch = window * args.steps
+    t_int = phase[1] / 1e3 / n_launch
+    achieved = alg_bytes / t_int / 1e9
+    peak, peak_kind = _measured_peaks()
+    traffic = _traffic_for(f"k_fused_{args.precision}", interior_nodes)
+
+    # e2e: host buffers through the C-ABI
+    e2e = None
+    if not args.no_e2e:
+        mat = np.ascontiguousarray(prob.mat)
+        Q = inf["n_bins"]
+        spec = np.zeros((inf["n_probes"], max(Q, 1), 2))
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        te0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            s.set_materials(mat)            # H2D of the node coefficient ids (+ host precompute)
+            s.step(window)
+            s.spectra_into(spec)            # D2H of the FP64 spectra (synchronises)
+        te1 = time.perf_counter()
+        et = te1 - te0
+        if world > 1:
+            t = torch.tensor([et], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            et = float(t.item())
+        pitch = ((prob.nx + 1 + 63) // 64) * 64
+        h2d = pitch * (prob.ny + 1) * (prob.nz + 1) + 256 * 16
+        e2e = {"value": float(cells) * window * args.e2e_steps * world / et / 1e9, "unit": "Gcell-updates/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec.nbytes),
+               "steps": args.e2e_steps,
+               "includes": "fdtd_set_materials (host precompute + H2D), fdtd_step, fdtd_probe_spectra (D2H)"}
+    s.close()
+
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Gcell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "fp32" else f"{args.precision}-storage/f32-compute",
+        "data": "synthetic (seeded board geometry, sources and probes)",
+        "config": {**_describe(prob, args.workload, window, args.precision),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "phase_ms_per_leapfrog_step": {k: round(v / n_launch, 5) for k, v in
+                                       zip(["slab_h", "interior", "slab_e", "post", "dft_total"], phase)},
+        "roofline": {"bound": "hbm", "kernel": "k_fused (interior + z-UPML columns, fused H+E)", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "peak_source": peak_kind,
+                     "bytes_per_unit": bytes_per_node, "units_per_launch": interior_nodes,
+                     "upml_aux_bytes_per_launch": 32 * upml_nodes, "algorithmic_bytes_per_launch": alg_bytes,
+                     "mean_launch_ms": round(t_int * 1e3, 5)},
+        "gpu_launches": int(args.steps * (window * 4 + 2)),
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "device_ms_in_timed_region": round(dev_ms, 3),
+    }
+    return out
+
+
+def cpu_baseline(args, sample_steps: int):
+    """FP64 oracle on the same full-size workload for a few steps."""
+    import oracle
+    prob = _workload(args.workload)
+    n = os.cpu_count() or 1
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.run(prob, n_steps=sample_steps, trace=True, dft=False, n_threads=n)
+    t1 = time.perf_counter()
+    # setup (edge permittivity, grading) is included: it is part of a solve
+    v = prob.cells * sample_steps / (t1 - t0) / 1e9
+    return {"value": round(v, 6), "unit": "Gcell-updates/s", "cores": n, "kind": "oracle",
+            "sample": f"{sample_steps} leapfrog steps of the full {prob.nx}x{prob.ny}x{prob.nz} grid "
+                      f"(FP64, OpenMP {n} threads, setup included)"}
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the FP64 oracle timed as it stands on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+    prob = _workload(args.workload)
+    n = os.cpu_count() or 1
+    oracle.build()
+    per = max(1, args.ref_sample_steps)
+    oracle.run(prob, n_steps=1, trace=True, dft=False, n_threads=n)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(prob, n_steps=per, trace=True, dft=False, n_threads=n)
+        times.append(time.perf_counter() - t0)
+    el = sum(times)
+    v = prob.cells * per * args.steps / el / 1e9
+    sample = (f"each step: {per} leapfrog steps of the full {prob.nx}x{prob.ny}x{prob.nz} grid "
+              f"(FP64 oracle, OpenMP {n} threads, setup included)")
+    return {"impl": "reference", "metric": METRIC, "value": round(v, 6), "unit": "Gcell-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded board geometry, sources and probes)",
+            "config": _describe(prob, args.workload, per, "fp64"),
+            "cpu_baseline": {"value": round(v, 6), "unit": "Gcell-updates/s", "cores": n, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(v, 6), "unit": "Gcell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="multilayer", choices=["small", "realistic", "multilayer", "multilayer_q"])
+    ap.add_argument("--window", type=int, default=200)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=6)
+    ap.add_argument("--ref-sample-steps", type=int, default=2)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+
+    world, rank, local = _dist()
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out = run_single(args, world, rank, local)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args, args.cpu_sample_steps)
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

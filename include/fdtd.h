@@ -1,0 +1,250 @@
+/*
+ * fdtd.h -- C-ABI of libfdtd.so: a 3D Yee-grid FDTD solver with a Gedney
+ * D/B-form UPML for PCB power/ground structures, computed by hand-written CUDA
+ * kernels for sm_103a (GB300).
+ *
+ * The method ("A Time Domain Approach to Power Integrity for Printed Circuit
+ * Boards"): Maxwell's curl equations on the Yee grid of Fig. 2, leapfrog in
+ * time (Model section), terminated by a uniaxial PML (Eqs. 1-4) graded by
+ * Eq. 5 and backed by a PEC wall; time step bounded by Eq. 7; power and
+ * ground planes are perfect conductors (tangential E = 0); excitation by the
+ * current pulse of Eq. 8; probe time series reduced to spectra (Results
+ * section: FFT of the ground-plane E_z).
+ *
+ * Conventions used by every call:
+ *  - Cells (i, j, k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz.  Volumes given by
+ *    the caller are [nz][ny][nx], x fastest.
+ *  - An E edge is named by the node it starts at and its direction:
+ *    (i, j, k, FDTD_X) is E_x(i+1/2, j, k), FDTD_Y is E_y(i, j+1/2, k),
+ *    FDTD_Z is E_z(i, j, k+1/2).  Node indices run 0..n (inclusive).
+ *  - Units: SI (metres, seconds, A/m^2, V/m).
+ *  - Host pointers are read during the call only (copied); the library owns
+ *    all device memory it allocates, and frees it in fdtd_destroy.
+ *  - Every call returns FDTD_OK (0) or a negative fdtd_status; none aborts or
+ *    throws.  Work is queued asynchronously on the context's stream: a CUDA
+ *    error raised by queued kernels is reported by the next call that
+ *    synchronises (fdtd_sync, fdtd_probe_spectra, fdtd_probe_trace,
+ *    fdtd_get_field, fdtd_diagnostics).
+ *  - A context is not thread-safe; use one context per host thread/stream.
+ */
+#ifndef FDTD_H
+#define FDTD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FDTD_OK = 0,
+    FDTD_EINVAL = -1,     /* invalid argument (message from fdtd_last_error) */
+    FDTD_ENOMEM = -2,     /* device or host allocation failed */
+    FDTD_ECUDA = -3,      /* a CUDA runtime call or kernel failed */
+    FDTD_EUNSTABLE = -4,  /* NaN/Inf detected in the fields */
+    FDTD_ETIMEOUT = -5,   /* a bounded device-side wait gave up */
+    FDTD_ESTATE = -6      /* call not valid in the context's current state */
+} fdtd_status;
+
+enum { FDTD_FP32 = 0, FDTD_FP16_STORE = 1, FDTD_BF16_STORE = 2 };
+enum { FDTD_WALL_PEC = 0, FDTD_WALL_PMC = 1 };
+enum { FDTD_X = 0, FDTD_Y = 1, FDTD_Z = 2 };
+enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, FDTD_HZ = 5 };
+
+typedef struct fdtd_ctx fdtd_ctx;      /* one board, owned by the library */
+typedef struct fdtd_batch fdtd_batch;  /* a set of boards stepped together */
+
+/* Grid (Model section; anisotropic cells, the paper's key modification of its
+ * base code).  dt <= 0 selects dt = courant * Eq. 7 with v = c. */
+typedef struct {
+    int nx, ny, nz;
+    double dx, dy, dz;
+    double courant;
+    double dt;
+} fdtd_grid;
+
+/* UPML (Eqs. 1-5): depth in cells on faces -x,+x,-y,+y,-z,+z; polynomial
+ * order m and kappa_max of Eq. 5; sigma_max = -(m+1) ln(R0) / (2 eta0 d) for
+ * a layer of thickness d.  wall[f] is the outer boundary of face f: PEC
+ * (tangential E = 0) or PMC (tangential H = 0); a face with depth > 0 must be
+ * PEC (the UPML is backed by a perfect conductor, Model section). */
+typedef struct {
+    int depth[6];
+    double m;
+    double R0;
+    double kappa_max;
+    int wall[6];
+} fdtd_boundary;
+
+/* PEC region (Results section: planes modelled as perfect conductors): the
+ * half-open cell range [i0,i1) x [j0,j1) x [k0,k1); every E edge on the
+ * closed node box [i0,i1] x [j0,j1] x [k0,k1] is held at zero.  k1 == k0
+ * gives a zero-thickness sheet on node plane k0. */
+typedef struct {
+    int i0, i1, j0, j1, k0, k1;
+} fdtd_box;
+
+/* Read-only facts about a context (for bindings and benchmarks). */
+typedef struct {
+    int nx, ny, nz;
+    double dt;                 /* seconds */
+    long long step;            /* leapfrog steps completed (device counter, synchronised read) */
+    int n_sources, n_probes;
+    int n_total_steps;         /* DFT length N set by fdtd_set_spectrum (0 if unset) */
+    int n_bins;                /* DFT bins q = 0..n_bins-1, f_q = q / (N dt) */
+    int precision;
+    long long interior_nodes;  /* nodes updated by the fused interior kernel */
+    long long fused_upml_nodes;/* of those, nodes in z-UPML planes (carry D~y, D~z, B~y, B~z) */
+    long long slab_nodes;      /* nodes updated by the UPML/boundary slab kernels */
+    long long device_bytes;    /* device memory held */
+    int n_combo;               /* distinct per-node E-coefficient triples */
+} fdtd_info_t;
+
+/* Create a board (Model section, Fig. 1).
+ *  grid      grid size, cell sizes [m], Courant number or explicit dt.
+ *  mat_ids   host [nz][ny][nx] material index per cell (copied).
+ *  eps_r     host [n_mat] relative permittivity per material (> 0).  The
+ *            permittivity of an E edge is the mean over the cells sharing it.
+ *  pec       host [n_pec] PEC boxes, or NULL if n_pec == 0.
+ *  pec_mask  optional host [nz][ny][nx]: nonzero cells are PEC (each acts as a
+ *            1x1x1 box); may be NULL.
+ *  bnd       UPML depths, grading and outer walls.
+ *  precision FDTD_FP32, FDTD_FP16_STORE or FDTD_BF16_STORE (fields stored in
+ *            16 bits with a power-of-two scale, arithmetic in FP32; UPML
+ *            auxiliary D/B always FP32).
+ *  stream    cudaStream_t the context enqueues on; NULL makes the library
+ *            create (and later destroy) its own non-blocking stream.
+ *  out       receives the context.
+ * Errors: FDTD_EINVAL for bad sizes or walls, more than 256 distinct edge
+ * coefficient triples, a PMC face with UPML; FDTD_ENOMEM; FDTD_ECUDA. */
+int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat,
+                const fdtd_box *pec, int n_pec, const uint8_t *pec_mask,
+                const fdtd_boundary *bnd, int precision, void *stream, fdtd_ctx **out);
+
+/* Add a current source (Eq. 8, square restored in the exponent):
+ * J(t) = J0 ((t - t0)/tau) exp(-((t - t0)/tau)^2) [A/m^2] on E edge
+ * (i, j, k, comp), applied at t = (n + 1/2) dt as E -= dt J / eps.  Several
+ * sources may share an edge (they add).  The edge must lie outside the UPML
+ * and must not be PEC (FDTD_EINVAL).  Only before the first fdtd_step
+ * (FDTD_ESTATE).  src_id may be NULL. */
+int fdtd_set_source(fdtd_ctx *ctx, int i, int j, int k, int comp, double J0, double t0, double tau,
+                    int *src_id);
+
+/* Add a probe on E edge (i, j, k, comp): samples E^{n+1} after every step
+ * (Results section: ground-plane E_z).  Only before the first fdtd_step. */
+int fdtd_add_probe(fdtd_ctx *ctx, int i, int j, int k, int comp, int *probe_id);
+
+/* Set the spectrum: the first n_total_steps samples of every probe are kept
+ * (FP32 trace) and accumulated into a running DFT in FP64,
+ * X_p(f_q) = dt sum_{n < N} x_p^n exp(-j 2 pi q n / N), f_q = q / (N dt),
+ * for f_q <= f_max (f_max <= 0: all bins up to Nyquist, N/2 + 1).  Samples
+ * after step N are not recorded.  Only before the first fdtd_step. */
+int fdtd_set_spectrum(fdtd_ctx *ctx, double f_max, int n_total_steps);
+
+/* Advance n >= 0 leapfrog steps (H^{n+1/2} from E^n, then E^{n+1} from
+ * H^{n+1/2} and J^{n+1/2}, then probes and DFT).  Asynchronous on the
+ * context's stream; fields stay on the device between calls. */
+int fdtd_step(fdtd_ctx *ctx, int n);
+
+/* fdtd_step with every phase launched directly (no CUDA graph) and timed
+ * with CUDA events on the context's stream: phase_ms[0..4] receive the summed
+ * device time [ms] of the UPML/boundary slab H kernel, the interior fused
+ * H+E kernel, the slab E kernel, the source/probe kernel and the running-DFT
+ * update over the n steps.  Synchronises.  phase_ms may not be NULL. */
+int fdtd_step_profiled(fdtd_ctx *ctx, int n, double *phase_ms);
+
+/* Copy the running DFT to host out[P][Q][2] (re, im), P = probes, Q = bins;
+ * requires max_bins >= Q.  *n_bins receives Q.  Synchronises the stream. */
+int fdtd_probe_spectra(fdtd_ctx *ctx, double *out, int max_bins, int *n_bins);
+
+/* Copy the FP32 trace of one probe (V/m, samples 0..len-1) to host out.
+ * *len receives min(recorded samples, max_len).  Synchronises. */
+int fdtd_probe_trace(fdtd_ctx *ctx, int probe, float *out, int max_len, int *len);
+
+/* Copy one field component to host out[(nz+1)(ny+1)(nx+1)] as FP32 in SI
+ * units (E in V/m, H in A/m), node layout [k][j][i]; entries where the
+ * component does not exist are 0.  field is FDTD_EX..FDTD_HZ; E is E^{n},
+ * H is H^{n-1/2} after n steps.  Synchronises. */
+int fdtd_get_field(fdtd_ctx *ctx, int field, float *out);
+
+/* Discrete energy W = 1/2 V (sum eps E^{n-1}.E^{n-1} + sum mu0 H^{n-3/2}.H^{n-1/2})
+ * of the last completed step (exactly conserved by the Yee scheme in a
+ * lossless closed box) and max |div B| [T/m] over cells outside the UPML,
+ * both reduced in FP64 on the device.  Needs at least one step.  Either
+ * output may be NULL.  Synchronises. */
+int fdtd_diagnostics(fdtd_ctx *ctx, double *energy, double *max_div_b);
+
+/* Zero all fields, UPML auxiliaries, traces, DFT accumulators and the step
+ * counter (sources, probes and geometry stay).  Asynchronous. */
+int fdtd_reset(fdtd_ctx *ctx);
+
+/* Replace the material ids of the board (same eps_r table, PEC and ports),
+ * copying host mat_ids [nz][ny][nx] to the device and rebuilding the edge
+ * coefficient ids, then reset.  Returns FDTD_EINVAL if the new geometry has
+ * more than 256 coefficient triples. */
+int fdtd_set_materials(fdtd_ctx *ctx, const uint8_t *mat_ids);
+
+/* Fill *info (synchronises to read the step counter). */
+int fdtd_info(fdtd_ctx *ctx, fdtd_info_t *info);
+
+/* Wait for all queued work; returns the first CUDA error or NaN/Inf found
+ * by the stability check (FDTD_EUNSTABLE). */
+int fdtd_sync(fdtd_ctx *ctx);
+
+/* Release the context and its device memory (synchronises first). */
+void fdtd_destroy(fdtd_ctx *ctx);
+
+/* Static text for a status code. */
+const char *fdtd_strerror(int code);
+
+/* Text of the last FDTD_EINVAL / FDTD_ECUDA raised on this host thread. */
+const char *fdtd_last_error(void);
+
+/* ---------------- batching (many boards, one launch per phase) -------------
+ * A batch steps many boards with one kernel launch per phase (UPML H, interior
+ * fused H+E, UPML E, sources/probes) over a packed list of (board, tile) work
+ * items, replayed as one CUDA graph per chunk of steps.  Each board's
+ * arithmetic is identical to stepping it alone.  Boards keep their own device
+ * state and may join or leave between calls.  All boards must share the
+ * batch's stream (the batch uses its own; member contexts must not be
+ * stepped on their own while in a batch). */
+
+/* Create an empty batch on stream (NULL: own stream). */
+int fdtd_batch_create(void *stream, fdtd_batch **out);
+
+/* Add a board that will run n_steps more steps (its ports and spectrum must
+ * be set).  FDTD_EINVAL if it is already in a batch. */
+int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *ctx, int n_steps);
+
+/* Remove a board (its state stays valid; synchronises the batch stream). */
+int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *ctx);
+
+/* Advance every member by min(n, its remaining steps); members that reach
+ * their target stop while the others continue.  *n_done (may be NULL)
+ * receives the number of members that have no steps left. */
+int fdtd_batch_step(fdtd_batch *b, int n, int *n_done);
+
+/* Remaining steps of one member (synchronises). */
+int fdtd_batch_remaining(fdtd_batch *b, fdtd_ctx *ctx, long long *remaining);
+
+/* Wait for the batch stream. */
+int fdtd_batch_sync(fdtd_batch *b);
+
+/* Destroy the batch (members stay alive and are detached). */
+void fdtd_batch_destroy(fdtd_batch *b);
+
+/* Tuning knobs of the kernels (autotuner): interior tile (tile_x threads in
+ * x, tile_y in y), z-segment length per thread and graph chunk.  Values <= 0
+ * keep the current setting.  Applies to launches queued afterwards. */
+typedef struct {
+    int tile_x, tile_y, zseg, graph_chunk;
+} fdtd_tuning;
+
+int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);
+int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FDTD_H */

@@ -1,0 +1,1180 @@
+// fdtd_capi.cu -- the C-ABI of libfdtd.so (declared in include/fdtd.h).
+//
+// Host side of the CUDA path: validates the problem, precomputes what the
+// kernels read (per-edge permittivity -> <=256-entry coefficient table +
+// uint8 id per node, Eq. 5 grading -> 1D UPML factors per axis, Eq. 7 time
+// step, slab decomposition of the UPML), owns device memory, captures chunks
+// of steps into CUDA graphs and batches boards into one launch per phase.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "../../include/fdtd.h"
+#include "fdtd_internal.h"
+
+using namespace fdtd;
+
+namespace {
+
+const double kC0 = 299792458.0;
+const double kMu0 = 4.0e-7 * 3.14159265358979323846;
+const double kEps0 = 1.0 / (kMu0 * kC0 * kC0);
+const double kEta0 = kMu0 * kC0;
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string &msg)
+{
+    g_err = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where)
+{
+    g_err = std::string(where) + ": " + cudaGetErrorString(e);
+    return FDTD_ECUDA;
+}
+
+#define CK(call)                                           \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+int elem_size(int prec) { return prec == FDTD_FP32 ? 4 : 2; }
+
+}  // namespace
+
+struct fdtd_batch;
+
+struct fdtd_ctx {
+    // problem
+    fdtd_grid g{};
+    fdtd_boundary bnd{};
+    std::vector<double> eps;
+    std::vector<fdtd_box> boxes;
+    std::vector<uint8_t> mask;
+    int prec = FDTD_FP32;
+    double dt = 0.0;
+    // host mirror of the device descriptor
+    Board h{};
+    Board *d = nullptr;
+    std::vector<void *> allocs;
+    std::vector<Source> src;
+    std::vector<Probe> probe;
+    std::vector<float4> ctab;
+    int n_combo = 0;
+    long long device_bytes = 0;
+    bool started = false;       // first step queued: sources/probes/scale frozen
+    bool own_stream = false;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cur = nullptr; // stream work is queued on (batch stream while batched)
+    long long host_step = 0;
+    fdtd_batch *batch = nullptr;
+    // single-board plan and graph
+    fdtd_tuning tune{32, 4, 16, 16};
+    bool plan_dirty = true;
+    Plan plan{};
+    long long *plan_buf = nullptr;   // device [0]=board ptr, then prefixes
+    size_t plan_cap = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    double *energy_buf = nullptr;    // partials + 2 outputs
+    int energy_n = 0;
+    int grid_cap = 0;
+    std::vector<cudaEvent_t> events; // fdtd_step_profiled
+    size_t zaux_n[2] = {0, 0};       // elements per fused-region z-UPML auxiliary array
+};
+
+struct fdtd_batch {
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<fdtd_ctx *> members;
+    std::vector<long long> remaining;
+    fdtd_tuning tune{32, 4, 16, 16};
+    bool dirty = true;
+    Plan plan{};
+    long long *plan_buf = nullptr;
+    size_t plan_cap = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_chunk = 0;
+    int prec = -1;
+    int grid_cap = 0;
+};
+
+namespace {
+
+int device_grid_cap()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1024;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) return 1024;
+    return sms * 8;
+}
+
+template <typename P>
+int dalloc(fdtd_ctx *c, P **out, size_t bytes)
+{
+    void *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FDTD_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(p);
+    c->device_bytes += (long long)bytes;
+    *out = (P *)p;
+    return FDTD_OK;
+}
+
+// Eq. 5 grading and the D/B recurrence factors at position x (cells) of an
+// axis with N cells, UPML depths dlo / dhi, cell size d.
+Coef upml_coef(double x, int N, int dlo, int dhi, double d, double m, double R0, double kmax, double dt)
+{
+    double rho = 0.0;
+    int depth = 0;
+    if (dlo > 0 && x < dlo) {
+        rho = (dlo - x) / dlo;
+        depth = dlo;
+    } else if (dhi > 0 && x > N - dhi) {
+        rho = (x - (N - dhi)) / dhi;
+        depth = dhi;
+    }
+    double sigma = 0.0, kappa = 1.0;
+    if (depth > 0) {
+        const double smax = -(m + 1.0) * std::log(R0) / (2.0 * kEta0 * depth * d);
+        const double r = std::pow(rho, m);
+        sigma = smax * r;
+        kappa = 1.0 + (kmax - 1.0) * r;
+    }
+    const double q = sigma * dt / (2.0 * kEps0);
+    Coef c;
+    c.b1 = (float)((kappa - q) / (kappa + q));
+    c.g = (float)(1.0 / (kappa + q));
+    c.ap = (float)(kappa + q);
+    c.am = (float)(kappa - q);
+    return c;
+}
+
+bool trivial(const Coef &c) { return c.b1 == 1.0f && c.g == 1.0f && c.ap == 1.0f && c.am == 1.0f; }
+
+struct Axes {
+    std::vector<Coef> cw[3][2];   // [axis][int/half][0..N]
+};
+
+void build_axes(const fdtd_ctx *c, Axes &A)
+{
+    const int N[3] = {c->g.nx, c->g.ny, c->g.nz};
+    const double D[3] = {c->g.dx, c->g.dy, c->g.dz};
+    for (int w = 0; w < 3; ++w) {
+        const int dlo = c->bnd.depth[2 * w], dhi = c->bnd.depth[2 * w + 1];
+        A.cw[w][0].resize(N[w] + 1);
+        A.cw[w][1].resize(N[w] + 1);
+        for (int i = 0; i <= N[w]; ++i) {
+            A.cw[w][0][i] = upml_coef((double)i, N[w], dlo, dhi, D[w], c->bnd.m, c->bnd.R0, c->bnd.kappa_max, c->dt);
+            A.cw[w][1][i] = i < N[w] ? upml_coef(i + 0.5, N[w], dlo, dhi, D[w], c->bnd.m, c->bnd.R0,
+                                                 c->bnd.kappa_max, c->dt)
+                                     : Coef{1.0f, 1.0f, 1.0f, 1.0f};
+        }
+    }
+}
+
+// Per-node coefficient ids: ce = 1/eps_r(edge) for the three edges starting at
+// the node (mean over the existing cells sharing the edge), 0 on PEC edges and
+// on edges that do not exist.  Returns the table (<= 65536 rows) and the
+// pitched id volume; the caller stores ids as uint8 when the table has at most
+// 256 rows.
+int build_combo(const fdtd_ctx *c, const uint8_t *mat, std::vector<uint16_t> &cid, std::vector<float4> &table)
+{
+    const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
+    const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
+    const int pitch = c->h.pitch;
+    for (size_t t = 0; t < (size_t)nx * ny * nz; ++t)
+        if (mat[t] >= c->eps.size()) return fail(FDTD_EINVAL, "material id out of range of eps_r");
+    // PEC edge bits per node: 1 = x edge, 2 = y edge, 4 = z edge
+    std::vector<uint8_t> pec((size_t)NX * NY * NZ, 0);
+    auto mark_box = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
+        for (int k = std::max(k0, 0); k <= std::min(k1, nz); ++k)
+            for (int j = std::max(j0, 0); j <= std::min(j1, ny); ++j)
+                for (int i = std::max(i0, 0); i <= std::min(i1, nx); ++i) {
+                    uint8_t bits = 0;
+                    if (i < i1 && i < nx) bits |= 1;
+                    if (j < j1 && j < ny) bits |= 2;
+                    if (k < k1 && k < nz) bits |= 4;
+                    pec[((size_t)k * NY + j) * NX + i] |= bits;
+                }
+    };
+    for (const fdtd_box &b : c->boxes) mark_box(b.i0, b.i1, b.j0, b.j1, b.k0, b.k1);
+    if (!c->mask.empty())
+        for (int k = 0; k < nz; ++k)
+            for (int j = 0; j < ny; ++j)
+                for (int i = 0; i < nx; ++i)
+                    if (c->mask[((size_t)k * ny + j) * nx + i]) mark_box(i, i + 1, j, j + 1, k, k + 1);
+    const int *wall = c->bnd.wall;
+
+    cid.assign((size_t)pitch * NY * NZ, 0);
+    std::vector<std::vector<float4>> plane_tab(NZ);
+    std::vector<int> overflow(NZ, 0);
+    std::vector<std::unordered_map<uint64_t, uint32_t>> plane_map(NZ);
+    auto eps_cell = [&](int i, int j, int k) { return c->eps[mat[((size_t)k * ny + j) * nx + i]]; };
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int k = 0; k < NZ; ++k) {
+        std::vector<float4> &tab = plane_tab[k];
+        std::unordered_map<uint64_t, uint32_t> &map = plane_map[k];
+        float4 last = make_float4(-1, -1, -1, 0);
+        uint16_t last_id = 0;
+        for (int j = 0; j < NY; ++j) {
+            for (int i = 0; i < NX; ++i) {
+                const uint8_t pb = pec[((size_t)k * NY + j) * NX + i];
+                const bool wx = (i == 0 && wall[0] == FDTD_WALL_PEC) || (i == nx && wall[1] == FDTD_WALL_PEC);
+                const bool wy = (j == 0 && wall[2] == FDTD_WALL_PEC) || (j == ny && wall[3] == FDTD_WALL_PEC);
+                const bool wz = (k == 0 && wall[4] == FDTD_WALL_PEC) || (k == nz && wall[5] == FDTD_WALL_PEC);
+                float ce[3] = {0.f, 0.f, 0.f};
+                if (i < nx && !(pb & 1) && !wy && !wz) {
+                    double s = 0; int n = 0;
+                    for (int b = k - 1; b <= k; ++b)
+                        for (int a = j - 1; a <= j; ++a)
+                            if (a >= 0 && a < ny && b >= 0 && b < nz) { s += eps_cell(i, a, b); ++n; }
+                    ce[0] = (float)(n / s);
+                }
+                if (j < ny && !(pb & 2) && !wx && !wz) {
+                    double s = 0; int n = 0;
+                    for (int b = k - 1; b <= k; ++b)
+                        for (int a = i - 1; a <= i; ++a)
+                            if (a >= 0 && a < nx && b >= 0 && b < nz) { s += eps_cell(a, j, b); ++n; }
+                    ce[1] = (float)(n / s);
+                }
+                if (k < nz && !(pb & 4) && !wx && !wy) {
+                    double s = 0; int n = 0;
+                    for (int b = j - 1; b <= j; ++b)
+                        for (int a = i - 1; a <= i; ++a)
+                            if (a >= 0 && a < nx && b >= 0 && b < ny) { s += eps_cell(a, b, k); ++n; }
+                    ce[2] = (float)(n / s);
+                }
+                const float4 v = make_float4(ce[0], ce[1], ce[2], 0.f);
+                uint16_t id;
+                if (v.x == last.x && v.y == last.y && v.z == last.z) {
+                    id = last_id;
+                } else {
+                    uint32_t bx, by, bz;
+                    std::memcpy(&bx, &v.x, 4); std::memcpy(&by, &v.y, 4); std::memcpy(&bz, &v.z, 4);
+                    // 64-bit key of the triple: exact when the plane's table stays small,
+                    // collisions are resolved by comparing the stored row
+                    const uint64_t key = ((uint64_t)bx * 0x9E3779B97F4A7C15ull) ^ ((uint64_t)by << 21) ^
+                                         ((uint64_t)bz * 0xC2B2AE3D27D4EB4Full);
+                    auto it = map.find(key);
+                    size_t t;
+                    if (it != map.end() && tab[it->second].x == v.x && tab[it->second].y == v.y &&
+                        tab[it->second].z == v.z) {
+                        t = it->second;
+                    } else {
+                        for (t = 0; t < tab.size(); ++t)
+                            if (tab[t].x == v.x && tab[t].y == v.y && tab[t].z == v.z) break;
+                        if (t == tab.size()) {
+                            if (tab.size() >= (size_t)kMaxCombo16) { overflow[k] = 1; t = 0; }
+                            else { tab.push_back(v); map[key] = (uint32_t)t; }
+                        }
+                    }
+                    id = (uint16_t)t;
+                    last = v;
+                    last_id = id;
+                }
+                cid[((size_t)k * NY + j) * pitch + i] = id;
+            }
+        }
+    }
+    for (int k = 0; k < NZ; ++k)
+        if (overflow[k]) return fail(FDTD_EINVAL, "more than 65536 distinct edge coefficient triples in one plane");
+    // merge plane tables into one global table, remap ids
+    table.clear();
+    std::unordered_map<uint64_t, std::vector<uint32_t>> gmap;
+    std::vector<std::vector<uint16_t>> remap(NZ);
+    for (int k = 0; k < NZ; ++k) {
+        for (const float4 &v : plane_tab[k]) {
+            uint32_t bx, by, bz;
+            std::memcpy(&bx, &v.x, 4); std::memcpy(&by, &v.y, 4); std::memcpy(&bz, &v.z, 4);
+            const uint64_t key = ((uint64_t)bx << 32) ^ ((uint64_t)by * 0x9E3779B97F4A7C15ull) ^ bz;
+            std::vector<uint32_t> &cands = gmap[key];
+            size_t t = table.size();
+            for (uint32_t cnd : cands)
+                if (table[cnd].x == v.x && table[cnd].y == v.y && table[cnd].z == v.z) { t = cnd; break; }
+            if (t == table.size()) {
+                if (table.size() >= (size_t)kMaxCombo16)
+                    return fail(FDTD_EINVAL, "more than 65536 distinct edge coefficient triples");
+                table.push_back(v);
+                cands.push_back((uint32_t)t);
+            }
+            remap[k].push_back((uint16_t)t);
+        }
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < NZ; ++k) {
+        uint16_t *row = cid.data() + (size_t)k * NY * pitch;
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i < NX; ++i) row[(size_t)j * pitch + i] = remap[k][row[(size_t)j * pitch + i]];
+    }
+    return FDTD_OK;
+}
+
+long long node_index(const Board &h, int i, int j, int k) { return (long long)k * h.plane + (long long)j * h.pitch + i; }
+
+bool edge_exists(const fdtd_ctx *c, int i, int j, int k, int comp)
+{
+    if (i < 0 || j < 0 || k < 0 || i > c->g.nx || j > c->g.ny || k > c->g.nz) return false;
+    if (comp == 0) return i < c->g.nx;
+    if (comp == 1) return j < c->g.ny;
+    if (comp == 2) return k < c->g.nz;
+    return false;
+}
+
+int upload_board(fdtd_ctx *c)
+{
+    CK(cudaMemcpyAsync(c->d, &c->h, sizeof(Board), cudaMemcpyHostToDevice, c->cur));
+    return FDTD_OK;
+}
+
+// Decide the storage scale, upload sources/probes/trace buffers and the
+// descriptor; called once before the first step.
+int finalize(fdtd_ctx *c)
+{
+    if (c->started) return FDTD_OK;
+    double s = 1.0;
+    if (c->prec != FDTD_FP32 && !c->src.empty()) {
+        double jmax = 0.0;
+        for (const Source &S : c->src) jmax = std::max(jmax, std::fabs(S.J0));
+        if (jmax > 0.0) s = std::exp2(std::ceil(std::log2(c->dt * jmax / kEps0)));
+    }
+    c->h.scale = (float)s;
+    for (Source &S : c->src) S.coef = S.coef / s;   // coef was stored as ce dt / eps0
+    if (!c->src.empty()) {
+        Source *d = nullptr;
+        if (int r = dalloc(c, &d, sizeof(Source) * c->src.size())) return r;
+        CK(cudaMemcpyAsync(d, c->src.data(), sizeof(Source) * c->src.size(), cudaMemcpyHostToDevice, c->cur));
+        c->h.src = d;
+    }
+    c->h.n_src = (int)c->src.size();
+    if (!c->probe.empty()) {
+        Probe *d = nullptr;
+        if (int r = dalloc(c, &d, sizeof(Probe) * c->probe.size())) return r;
+        CK(cudaMemcpyAsync(d, c->probe.data(), sizeof(Probe) * c->probe.size(), cudaMemcpyHostToDevice, c->cur));
+        c->h.probe = d;
+    }
+    c->h.n_probe = (int)c->probe.size();
+    if (c->h.n_total > 0 && c->h.n_probe > 0) {
+        float *tr = nullptr;
+        double *dft = nullptr;
+        if (int r = dalloc(c, &tr, sizeof(float) * (size_t)c->h.n_probe * c->h.n_total)) return r;
+        if (int r = dalloc(c, &dft, sizeof(double) * 2 * (size_t)c->h.n_probe * std::max(c->h.n_bins, 1))) return r;
+        CK(cudaMemsetAsync(tr, 0, sizeof(float) * (size_t)c->h.n_probe * c->h.n_total, c->cur));
+        CK(cudaMemsetAsync(dft, 0, sizeof(double) * 2 * (size_t)c->h.n_probe * std::max(c->h.n_bins, 1), c->cur));
+        c->h.trace = tr;
+        c->h.dft = dft;
+    }
+    c->started = true;
+    c->plan_dirty = true;
+    return upload_board(c);
+}
+
+long long interior_items(const Board &h, const fdtd_tuning &t)
+{
+    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
+    if (Lx <= 0 || Ly <= 0 || Lz <= 0) return 0;
+    return ((Lx + 31) / 32) * ((Ly + t.tile_y - 1) / t.tile_y) * ((Lz + t.zseg - 1) / t.zseg);
+}
+
+long long dft_items(const Board &h)
+{
+    if (h.n_total <= 0 || h.n_probe <= 0) return 0;
+    return (long long)h.n_bins * ((h.n_probe + kDftProbeGroup - 1) / kDftProbeGroup);
+}
+
+// Lay out plan arrays [boards | int_prefix | slab_prefix | dft_prefix] in buf.
+int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long long *&buf, size_t &cap,
+               Plan &plan, cudaStream_t st, std::vector<long long> &host)
+{
+    const int nb = (int)boards.size();
+    const size_t words = (size_t)nb + 3 * ((size_t)nb + 1);
+    host.assign(words, 0);
+    long long *ptrs = host.data();
+    long long *ip = ptrs + nb, *sp = ip + nb + 1, *dp = sp + nb + 1;
+    for (int b = 0; b < nb; ++b) {
+        ptrs[b] = (long long)(uintptr_t)boards[b]->d;
+        ip[b + 1] = ip[b] + interior_items(boards[b]->h, t);
+        sp[b + 1] = sp[b] + boards[b]->h.slab_blocks;
+        dp[b + 1] = dp[b] + dft_items(boards[b]->h);
+    }
+    if (words > cap) {
+        if (buf) cudaFree(buf);
+        buf = nullptr;
+        cap = 0;
+        cudaError_t e = cudaMalloc(&buf, words * sizeof(long long));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(FDTD_ENOMEM, "plan allocation failed");
+        }
+        cap = words;
+    }
+    CK(cudaMemcpyAsync(buf, host.data(), words * sizeof(long long), cudaMemcpyHostToDevice, st));
+    plan.nb = nb;
+    plan.tile_x = t.tile_x;
+    plan.tile_y = t.tile_y;
+    plan.zseg = t.zseg;
+    plan.boards = (Board *const *)buf;
+    plan.int_prefix = buf + nb;
+    plan.slab_prefix = buf + nb + (nb + 1);
+    plan.dft_prefix = buf + nb + 2 * (nb + 1);
+    plan.n_int = ip[nb];
+    plan.n_slab = sp[nb];
+    plan.n_dft = dp[nb];
+    return FDTD_OK;
+}
+
+// Run n steps of `plan` on stream st: CUDA graphs of `chunk` steps (each
+// ending with the running-DFT update), direct launches for the remainder.
+int run_steps(const Plan &plan, int prec, int grid_cap, int n, int chunk, cudaGraphExec_t &graph, int &graph_chunk,
+              cudaStream_t st)
+{
+    if (n <= 0) return FDTD_OK;
+    if (chunk > 1 && n >= chunk) {
+        if (!graph || graph_chunk != chunk) {
+            if (graph) cudaGraphExecDestroy(graph);
+            graph = nullptr;
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int s = 0; s < chunk && e == cudaSuccess; ++s) e = launch_step(plan, prec, grid_cap, st);
+            if (e == cudaSuccess) e = launch_dft(plan, grid_cap, st);
+            cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+            if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&graph, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) { graph = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+            graph_chunk = chunk;
+        }
+        for (int r = 0; r < n / chunk; ++r) CK(cudaGraphLaunch(graph, st));
+        n %= chunk;
+    }
+    if (n > 0) {
+        for (int s = 0; s < n; ++s) CK(launch_step(plan, prec, grid_cap, st));
+        CK(launch_dft(plan, grid_cap, st));
+    }
+    return FDTD_OK;
+}
+
+int check_status(fdtd_ctx *c)
+{
+    int st = 0;
+    CK(cudaMemcpy(&st, c->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 1) return fail(FDTD_EUNSTABLE, "non-finite probe sample (unstable run: check the Courant number)");
+    return FDTD_OK;
+}
+
+int set_geometry(fdtd_ctx *c, const uint8_t *mat)
+{
+    std::vector<uint16_t> cid;
+    std::vector<float4> table;
+    if (int r = build_combo(c, mat, cid, table)) return r;
+    c->n_combo = (int)table.size();
+    const int id16 = table.size() > (size_t)kMaxCombo ? 1 : 0;
+    const size_t rows = id16 ? (size_t)kMaxCombo16 : (size_t)kMaxCombo;
+    table.resize(rows, make_float4(0, 0, 0, 0));
+    c->ctab = table;
+    if (id16 != c->h.id16 || !c->h.cid) {
+        // id buffers of the other width: allocate once, kept until destroy
+        void *d = nullptr;
+        float4 *t = nullptr;
+        if (int r = dalloc(c, &d, (size_t)c->h.nodes * (id16 ? 2 : 1))) return r;
+        if (int r = dalloc(c, &t, sizeof(float4) * rows)) return r;
+        c->h.cid = d;
+        c->h.ctab = t;
+        c->h.id16 = id16;
+        c->plan_dirty = true;
+    }
+    if (id16) {
+        CK(cudaMemcpyAsync((void *)c->h.cid, cid.data(), cid.size() * 2, cudaMemcpyHostToDevice, c->cur));
+        CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
+        CK(cudaStreamSynchronize(c->cur));
+    } else {
+        std::vector<uint8_t> c8(cid.size());
+#pragma omp parallel for schedule(static)
+        for (long long t = 0; t < (long long)cid.size(); ++t) c8[t] = (uint8_t)cid[t];
+        CK(cudaMemcpyAsync((void *)c->h.cid, c8.data(), c8.size(), cudaMemcpyHostToDevice, c->cur));
+        CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
+        // the host copies stay alive until the copies finish
+        CK(cudaStreamSynchronize(c->cur));
+    }
+    if (c->d) return upload_board(c);
+    return FDTD_OK;
+}
+
+uint32_t edge_combo(const fdtd_ctx *c, long long node)
+{
+    uint32_t id = 0;
+    if (c->h.id16) {
+        uint16_t v = 0;
+        cudaMemcpy(&v, (const uint16_t *)c->h.cid + node, 2, cudaMemcpyDeviceToHost);
+        id = v;
+    } else {
+        uint8_t v = 0;
+        cudaMemcpy(&v, (const uint8_t *)c->h.cid + node, 1, cudaMemcpyDeviceToHost);
+        id = v;
+    }
+    return id;
+}
+
+}  // namespace
+
+// =========================================================================== C-ABI
+
+extern "C" {
+
+const char *fdtd_strerror(int code)
+{
+    switch (code) {
+    case FDTD_OK: return "ok";
+    case FDTD_EINVAL: return "invalid argument";
+    case FDTD_ENOMEM: return "out of memory";
+    case FDTD_ECUDA: return "CUDA error";
+    case FDTD_EUNSTABLE: return "unstable (non-finite field values)";
+    case FDTD_ETIMEOUT: return "device wait timed out";
+    case FDTD_ESTATE: return "call not valid in the current state";
+    default: return "unknown status";
+    }
+}
+
+const char *fdtd_last_error(void) { return g_err.c_str(); }
+
+void fdtd_destroy(fdtd_ctx *c);
+
+int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat, const fdtd_box *pec,
+                int n_pec, const uint8_t *pec_mask, const fdtd_boundary *bnd, int precision, void *stream,
+                fdtd_ctx **out)
+{
+    if (!out) return fail(FDTD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !mat_ids || !eps_r || !bnd) return fail(FDTD_EINVAL, "NULL grid, mat_ids, eps_r or boundary");
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(FDTD_EINVAL, "grid must have at least one cell per axis");
+    if (!(grid->dx > 0 && grid->dy > 0 && grid->dz > 0)) return fail(FDTD_EINVAL, "cell sizes must be positive");
+    if (grid->dt <= 0 && !(grid->courant > 0)) return fail(FDTD_EINVAL, "need dt > 0 or courant > 0");
+    if (n_mat < 1 || n_mat > 256) return fail(FDTD_EINVAL, "n_mat must be in 1..256");
+    for (int m = 0; m < n_mat; ++m)
+        if (!(eps_r[m] > 0)) return fail(FDTD_EINVAL, "eps_r must be positive");
+    if (n_pec < 0 || (n_pec > 0 && !pec)) return fail(FDTD_EINVAL, "bad PEC box list");
+    if (precision < FDTD_FP32 || precision > FDTD_BF16_STORE) return fail(FDTD_EINVAL, "bad precision");
+    const int N[3] = {grid->nx, grid->ny, grid->nz};
+    for (int f = 0; f < 6; ++f) {
+        if (bnd->depth[f] < 0 || bnd->depth[f] > N[f / 2]) return fail(FDTD_EINVAL, "bad UPML depth");
+        if (bnd->wall[f] != FDTD_WALL_PEC && bnd->wall[f] != FDTD_WALL_PMC) return fail(FDTD_EINVAL, "bad wall type");
+        if (bnd->depth[f] > 0 && bnd->wall[f] != FDTD_WALL_PEC)
+            return fail(FDTD_EINVAL, "a face with UPML must be backed by a PEC wall");
+    }
+    for (int w = 0; w < 3; ++w)
+        if (bnd->depth[2 * w] + bnd->depth[2 * w + 1] > N[w]) return fail(FDTD_EINVAL, "UPML layers overlap");
+    if (bnd->depth[0] + bnd->depth[1] + bnd->depth[2] + bnd->depth[3] + bnd->depth[4] + bnd->depth[5] > 0 &&
+        !(bnd->R0 > 0 && bnd->R0 <= 1 && bnd->m >= 0 && bnd->kappa_max >= 1))
+        return fail(FDTD_EINVAL, "UPML needs 0 < R0 <= 1, m >= 0, kappa_max >= 1");
+
+    fdtd_ctx *c = new fdtd_ctx();
+    c->g = *grid;
+    c->bnd = *bnd;
+    c->eps.assign(eps_r, eps_r + n_mat);
+    if (n_pec > 0) c->boxes.assign(pec, pec + n_pec);
+    if (pec_mask) c->mask.assign(pec_mask, pec_mask + (size_t)grid->nx * grid->ny * grid->nz);
+    c->prec = precision;
+    c->dt = grid->dt > 0 ? grid->dt
+                         : grid->courant / (kC0 * std::sqrt(1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dy * grid->dy) +
+                                                             1.0 / (grid->dz * grid->dz)));
+    c->grid_cap = device_grid_cap();
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaStreamCreate"); }
+        c->own_stream = true;
+    }
+    c->cur = c->stream;
+
+    Board &h = c->h;
+    h.nx = grid->nx; h.ny = grid->ny; h.nz = grid->nz;
+    h.pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    h.plane = (long long)h.pitch * (grid->ny + 1);
+    h.nodes = h.plane * (grid->nz + 1);
+    if (h.nodes >= (1LL << 31)) { fdtd_destroy(c); return fail(FDTD_EINVAL, "grid too large (>= 2^31 nodes)"); }
+    h.prec = precision;
+    h.S[0] = (float)(kC0 * c->dt / grid->dx);
+    h.S[1] = (float)(kC0 * c->dt / grid->dy);
+    h.S[2] = (float)(kC0 * c->dt / grid->dz);
+    h.scale = 1.0f;
+    h.dt = c->dt;
+    for (int f = 0; f < 6; ++f) { h.wall[f] = bnd->wall[f]; h.depth[f] = bnd->depth[f]; }
+
+    int r = FDTD_OK;
+    const size_t fbytes = (size_t)h.nodes * elem_size(precision);
+    for (int p = 0; p < 2 && !r; ++p)
+        for (int f = 0; f < 6 && !r; ++f) {
+            r = dalloc(c, &h.f[p][f], fbytes);
+            if (!r) { cudaError_t e = cudaMemsetAsync(h.f[p][f], 0, fbytes, c->cur); if (e) r = cuda_fail(e, "memset"); }
+        }
+    h.cid = nullptr;
+    h.ctab = nullptr;
+    h.id16 = -1;
+    if (r) { fdtd_destroy(c); return r; }
+    if ((r = set_geometry(c, mat_ids))) { fdtd_destroy(c); return r; }
+
+    // UPML factors
+    Axes A;
+    build_axes(c, A);
+    for (int w = 0; w < 3 && !r; ++w)
+        for (int s = 0; s < 2 && !r; ++s) {
+            Coef *d = nullptr;
+            r = dalloc(c, &d, sizeof(Coef) * A.cw[w][s].size());
+            if (!r) {
+                cudaError_t e = cudaMemcpyAsync(d, A.cw[w][s].data(), sizeof(Coef) * A.cw[w][s].size(),
+                                                cudaMemcpyHostToDevice, c->cur);
+                if (e) r = cuda_fail(e, "upload UPML factors");
+            }
+            h.cw[w][s] = d;
+        }
+    if (r) { fdtd_destroy(c); return r; }
+
+    // fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) and the slabs around it
+    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
+    h.ix0 = std::max(bnd->depth[0], 1); h.ix1 = nx - bnd->depth[1];
+    h.iy0 = std::max(bnd->depth[2], 1); h.iy1 = ny - bnd->depth[3];
+    h.iz0 = std::max(bnd->depth[4], 1); h.iz1 = nz - bnd->depth[5];
+    std::vector<std::array<int, 6>> boxes;
+    const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
+    if (!fused) {
+        h.ix0 = h.ix1 = h.iy0 = h.iy1 = 0;
+        h.iz0 = 1; h.iz1 = nz;
+        boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
+    } else {
+        boxes.push_back({0, nx + 1, 0, ny + 1, 0, 1});
+        boxes.push_back({0, nx + 1, 0, ny + 1, nz, nz + 1});
+        boxes.push_back({0, nx + 1, 0, h.iy0, 1, nz});
+        boxes.push_back({0, nx + 1, h.iy1, ny + 1, 1, nz});
+        boxes.push_back({0, h.ix0, h.iy0, h.iy1, 1, nz});
+        boxes.push_back({h.ix1, nx + 1, h.iy0, h.iy1, 1, nz});
+    }
+    h.n_slab = 0;
+    int blocks = 0;
+    for (const auto &bx : boxes) {
+        if (bx[1] <= bx[0] || bx[3] <= bx[2] || bx[5] <= bx[4]) continue;
+        Slab &sl = h.slab[h.n_slab++];
+        sl.i0 = bx[0]; sl.i1 = bx[1]; sl.j0 = bx[2]; sl.j1 = bx[3]; sl.k0 = bx[4]; sl.k1 = bx[5];
+        sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
+        sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
+        sl.block0 = blocks;
+        blocks += (int)((sl.n + kSlabThreads - 1) / kSlabThreads);
+        const int lo[3] = {sl.i0, sl.j0, sl.k0}, hi[3] = {sl.i1, sl.j1, sl.k1};
+        auto any_nontrivial = [&](int axis, int half, bool need_b1g, bool need_apam) {
+            for (int t = lo[axis]; t < hi[axis]; ++t) {
+                const Coef &cf = A.cw[axis][half][t];
+                if (need_b1g && (cf.b1 != 1.0f || cf.g != 1.0f)) return true;
+                if (need_apam && (cf.ap != 1.0f || cf.am != 1.0f)) return true;
+            }
+            return false;
+        };
+        for (int comp = 0; comp < 6; ++comp) {
+            const int w = comp % 3, w1 = (w + 1) % 3;
+            const bool is_h = comp >= 3;
+            // E: D recurrence along w1 (integer), D->E along w (half)
+            // H: B recurrence along w1 (half),    B->H along w (integer)
+            const bool need = any_nontrivial(w1, is_h ? 1 : 0, true, false) ||
+                              any_nontrivial(w, is_h ? 0 : 1, false, true);
+            sl.aux[comp] = nullptr;
+            if (need && !r) {
+                r = dalloc(c, &sl.aux[comp], sizeof(float) * (size_t)sl.n);
+                if (!r) { cudaError_t e = cudaMemsetAsync(sl.aux[comp], 0, sizeof(float) * (size_t)sl.n, c->cur); if (e) r = cuda_fail(e, "memset"); }
+            }
+        }
+    }
+    // z-UPML auxiliaries of the fused region: lower box planes [1, iz0), upper [iz1, nz)
+    for (int bx = 0; bx < 2; ++bx) {
+        for (int a = 0; a < 2; ++a) {
+            h.zD[bx][a] = nullptr;
+            h.zB[bx][a][0] = h.zB[bx][a][1] = nullptr;
+        }
+        if (!fused) continue;
+        const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
+        if (planes <= 0) continue;
+        const size_t n = (size_t)planes * (h.ix1 - h.ix0) * (h.iy1 - h.iy0);
+        for (int a = 0; a < 2 && !r; ++a) {
+            float *ptr[3] = {nullptr, nullptr, nullptr};
+            for (int t = 0; t < 3 && !r; ++t) {
+                r = dalloc(c, &ptr[t], sizeof(float) * n);
+                if (!r) { cudaError_t e = cudaMemsetAsync(ptr[t], 0, sizeof(float) * n, c->cur); if (e) r = cuda_fail(e, "memset"); }
+            }
+            h.zD[bx][a] = ptr[0];
+            h.zB[bx][a][0] = ptr[1];
+            h.zB[bx][a][1] = ptr[2];
+        }
+        c->zaux_n[bx] = n;
+    }
+    h.slab_blocks = blocks;
+    long long *ctr = nullptr;
+    const long long init[4] = {0, LLONG_MAX, 0, 0};
+    if (!r) r = dalloc(c, &ctr, 4 * sizeof(long long));
+    if (!r) {
+        h.step = ctr; h.stop = ctr + 1; h.dft_done = ctr + 2; h.status = (int *)(ctr + 3);
+        cudaError_t e = cudaMemcpyAsync(ctr, init, sizeof(init), cudaMemcpyHostToDevice, c->cur);
+        if (e) r = cuda_fail(e, "init counters");
+    }
+    if (!r) r = dalloc(c, &c->d, sizeof(Board));
+    if (!r) {
+        c->energy_n = energy_partials(h);
+        r = dalloc(c, &c->energy_buf, sizeof(double) * (2 * (size_t)c->energy_n + 2));
+    }
+    if (!r) r = upload_board(c);
+    if (!r) { cudaError_t e = cudaStreamSynchronize(c->cur); if (e) r = cuda_fail(e, "create sync"); }
+    if (r) { fdtd_destroy(c); return r; }
+    *out = c;
+    return FDTD_OK;
+}
+
+int fdtd_set_source(fdtd_ctx *c, int i, int j, int k, int comp, double J0, double t0, double tau, int *src_id)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->started) return fail(FDTD_ESTATE, "sources must be added before the first step");
+    if (!edge_exists(c, i, j, k, comp)) return fail(FDTD_EINVAL, "source edge does not exist");
+    if (!(tau > 0)) return fail(FDTD_EINVAL, "tau must be positive");
+    // the edge must be outside the UPML: all three factors trivial at its position
+    Axes A;
+    build_axes(c, A);
+    const int idx[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a)
+        if (!trivial(A.cw[a][a == comp ? 1 : 0][idx[a]]))
+            return fail(FDTD_EINVAL, "source edge lies inside the UPML");
+    const float4 row = c->ctab[edge_combo(c, node_index(c->h, i, j, k))];
+    const float ce = comp == 0 ? row.x : comp == 1 ? row.y : row.z;
+    if (ce == 0.0f) return fail(FDTD_EINVAL, "source edge is PEC");
+    Source S{};
+    S.node = node_index(c->h, i, j, k);
+    S.comp = comp;
+    S.J0 = J0; S.t0 = t0; S.tau = tau;
+    S.coef = (double)ce * c->dt / kEps0;
+    c->src.push_back(S);
+    if (src_id) *src_id = (int)c->src.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_add_probe(fdtd_ctx *c, int i, int j, int k, int comp, int *probe_id)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->started) return fail(FDTD_ESTATE, "probes must be added before the first step");
+    if (!edge_exists(c, i, j, k, comp)) return fail(FDTD_EINVAL, "probe edge does not exist");
+    Probe p{};
+    p.node = node_index(c->h, i, j, k);
+    p.comp = comp;
+    c->probe.push_back(p);
+    if (probe_id) *probe_id = (int)c->probe.size() - 1;
+    return FDTD_OK;
+}
+
+int fdtd_set_spectrum(fdtd_ctx *c, double f_max, int n_total_steps)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->started) return fail(FDTD_ESTATE, "spectrum must be set before the first step");
+    if (n_total_steps < 1) return fail(FDTD_EINVAL, "n_total_steps must be >= 1");
+    const int nyq = n_total_steps / 2 + 1;
+    int Q = nyq;
+    if (f_max > 0) Q = std::min(nyq, (int)std::floor(f_max * n_total_steps * c->dt + 1e-9) + 1);
+    c->h.n_total = n_total_steps;
+    c->h.n_bins = Q;
+    return FDTD_OK;
+}
+
+int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t)
+{
+    if (!c || !t) return fail(FDTD_EINVAL, "NULL argument");
+    fdtd_tuning n = c->tune;
+    if (t->tile_x > 0) n.tile_x = t->tile_x;
+    if (t->tile_y > 0) n.tile_y = t->tile_y;
+    if (t->zseg > 0) n.zseg = t->zseg;
+    if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
+    if (n.tile_x != 32 || (n.tile_y != 2 && n.tile_y != 4 && n.tile_y != 8))
+        return fail(FDTD_EINVAL, "fused tile is 32 x tile_y with tile_y in {2, 4, 8}");
+    c->tune = n;
+    c->plan_dirty = true;
+    return FDTD_OK;
+}
+
+static int prepare_single(fdtd_ctx *c);
+
+int fdtd_step(fdtd_ctx *c, int n)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (n < 0) return fail(FDTD_EINVAL, "n must be >= 0");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; step the batch");
+    if (int r = prepare_single(c)) return r;
+    if (int r = run_steps(c->plan, c->prec, c->grid_cap, n, c->tune.graph_chunk, c->graph, c->graph_chunk, c->cur))
+        return r;
+    c->host_step += n;
+    return FDTD_OK;
+}
+
+static int prepare_single(fdtd_ctx *c)
+{
+    if (int r = finalize(c)) return r;
+    if (c->plan_dirty) {
+        std::vector<long long> host;
+        std::vector<fdtd_ctx *> one{c};
+        if (int r = build_plan(one, c->tune, c->plan_buf, c->plan_cap, c->plan, c->cur, host)) return r;
+        CK(cudaStreamSynchronize(c->cur));
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        c->plan_dirty = false;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_step_profiled(fdtd_ctx *c, int n, double *phase_ms)
+{
+    if (!c || !phase_ms) return fail(FDTD_EINVAL, "NULL argument");
+    if (n < 0) return fail(FDTD_EINVAL, "n must be >= 0");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; step the batch");
+    if (int r = prepare_single(c)) return r;
+    const size_t need = (size_t)n * (kNumPhases + 1) + 2;
+    while (c->events.size() < need) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        c->events.push_back(e);
+    }
+    for (int p = 0; p <= kNumPhases; ++p) phase_ms[p] = 0.0;
+    size_t ev = 0;
+    for (int s = 0; s < n; ++s) {
+        CK(cudaEventRecord(c->events[ev++], c->cur));
+        for (int ph = 0; ph < kNumPhases; ++ph) {
+            CK(launch_phase(c->plan, c->prec, ph, c->grid_cap, c->cur));
+            CK(cudaEventRecord(c->events[ev++], c->cur));
+        }
+    }
+    CK(cudaEventRecord(c->events[ev++], c->cur));
+    CK(launch_dft(c->plan, c->grid_cap, c->cur));
+    CK(cudaEventRecord(c->events[ev++], c->cur));
+    CK(cudaStreamSynchronize(c->cur));
+    ev = 0;
+    for (int s = 0; s < n; ++s) {
+        for (int ph = 0; ph < kNumPhases; ++ph) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, c->events[ev + ph], c->events[ev + ph + 1]));
+            phase_ms[ph] += ms;
+        }
+        ev += kNumPhases + 1;
+    }
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->events[ev], c->events[ev + 1]));
+    phase_ms[kNumPhases] += ms;
+    c->host_step += n;
+    return check_status(c);
+}
+
+int fdtd_sync(fdtd_ctx *c)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    CK(cudaStreamSynchronize(c->cur));
+    return check_status(c);
+}
+
+int fdtd_probe_spectra(fdtd_ctx *c, double *out, int max_bins, int *n_bins)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (n_bins) *n_bins = c->h.n_bins;
+    if (int r = fdtd_sync(c)) return r;
+    if (c->h.n_total <= 0 || c->h.n_probe <= 0 || !c->h.dft) return FDTD_OK;
+    if (!out || max_bins < c->h.n_bins) return fail(FDTD_EINVAL, "output too small for the spectrum");
+    CK(cudaMemcpy(out, c->h.dft, sizeof(double) * 2 * (size_t)c->h.n_probe * c->h.n_bins, cudaMemcpyDeviceToHost));
+    return FDTD_OK;
+}
+
+int fdtd_probe_trace(fdtd_ctx *c, int probe, float *out, int max_len, int *len)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (probe < 0 || probe >= (int)c->probe.size()) return fail(FDTD_EINVAL, "bad probe index");
+    if (int r = fdtd_sync(c)) return r;
+    long long n = std::min<long long>(c->host_step, c->h.n_total);
+    n = std::min<long long>(n, max_len);
+    if (len) *len = (int)n;
+    if (n <= 0 || !c->h.trace) return FDTD_OK;
+    if (!out) return fail(FDTD_EINVAL, "NULL output");
+    CK(cudaMemcpy(out, c->h.trace + (size_t)probe * c->h.n_total, sizeof(float) * n, cudaMemcpyDeviceToHost));
+    return FDTD_OK;
+}
+
+int fdtd_get_field(fdtd_ctx *c, int field, float *out)
+{
+    if (!c || !out) return fail(FDTD_EINVAL, "NULL argument");
+    if (field < 0 || field > 5) return fail(FDTD_EINVAL, "field must be 0..5");
+    if (int r = fdtd_sync(c)) return r;
+    const Board &h = c->h;
+    const int par = (int)(c->host_step & 1);
+    const int es = elem_size(c->prec);
+    std::vector<unsigned char> buf((size_t)h.nodes * es);
+    CK(cudaMemcpy(buf.data(), h.f[par][field], buf.size(), cudaMemcpyDeviceToHost));
+    const double s = field < 3 ? h.scale : h.scale / kEta0;
+    const int NX = h.nx + 1, NY = h.ny + 1, NZ = h.nz + 1;
+    for (int k = 0; k < NZ; ++k)
+        for (int j = 0; j < NY; ++j)
+            for (int i = 0; i < NX; ++i) {
+                const size_t src = ((size_t)k * NY + j) * h.pitch + i;
+                float v;
+                if (c->prec == FDTD_FP32) v = ((const float *)buf.data())[src];
+                else if (c->prec == FDTD_FP16_STORE) v = __half2float(((const __half *)buf.data())[src]);
+                else v = __bfloat162float(((const __nv_bfloat16 *)buf.data())[src]);
+                out[((size_t)k * NY + j) * NX + i] = (float)(v * s);
+            }
+    return FDTD_OK;
+}
+
+int fdtd_diagnostics(fdtd_ctx *c, double *energy, double *max_div_b)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->host_step < 1) return fail(FDTD_ESTATE, "diagnostics need at least one completed step");
+    double *part = c->energy_buf, *res = c->energy_buf + 2 * (size_t)c->energy_n;
+    CK(launch_energy(c->d, c->h, part, c->energy_n, res, c->cur));
+    if (int r = fdtd_sync(c)) return r;
+    double two[2];
+    CK(cudaMemcpy(two, res, sizeof(two), cudaMemcpyDeviceToHost));
+    const double s = c->h.scale;
+    if (energy) *energy = 0.5 * kEps0 * c->g.dx * c->g.dy * c->g.dz * s * s * two[0];
+    if (max_div_b) *max_div_b = s / (kC0 * kC0 * c->dt) * two[1];
+    return FDTD_OK;
+}
+
+int fdtd_reset(fdtd_ctx *c)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    Board &h = c->h;
+    const size_t fbytes = (size_t)h.nodes * elem_size(c->prec);
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 6; ++f) CK(cudaMemsetAsync(h.f[p][f], 0, fbytes, c->cur));
+    for (int s = 0; s < h.n_slab; ++s)
+        for (int a = 0; a < 6; ++a)
+            if (h.slab[s].aux[a]) CK(cudaMemsetAsync(h.slab[s].aux[a], 0, sizeof(float) * (size_t)h.slab[s].n, c->cur));
+    for (int bx = 0; bx < 2; ++bx)
+        for (int a = 0; a < 2; ++a) {
+            if (h.zD[bx][a]) CK(cudaMemsetAsync(h.zD[bx][a], 0, sizeof(float) * c->zaux_n[bx], c->cur));
+            for (int p = 0; p < 2; ++p)
+                if (h.zB[bx][a][p]) CK(cudaMemsetAsync(h.zB[bx][a][p], 0, sizeof(float) * c->zaux_n[bx], c->cur));
+        }
+    if (h.trace) CK(cudaMemsetAsync(h.trace, 0, sizeof(float) * (size_t)h.n_probe * h.n_total, c->cur));
+    if (h.dft) CK(cudaMemsetAsync(h.dft, 0, sizeof(double) * 2 * (size_t)h.n_probe * std::max(h.n_bins, 1), c->cur));
+    CK(cudaMemsetAsync(h.step, 0, sizeof(long long), c->cur));
+    CK(cudaMemsetAsync(h.dft_done, 0, sizeof(long long), c->cur));
+    CK(cudaMemsetAsync(h.status, 0, sizeof(int), c->cur));
+    c->host_step = 0;
+    return FDTD_OK;
+}
+
+int fdtd_set_materials(fdtd_ctx *c, const uint8_t *mat_ids)
+{
+    if (!c || !mat_ids) return fail(FDTD_EINVAL, "NULL argument");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch");
+    const std::vector<float4> old = c->ctab;
+    if (int r = set_geometry(c, mat_ids)) return r;
+    // sources keep their edge; refresh their coefficient for the new permittivity
+    if (!c->src.empty()) {
+        for (Source &S : c->src) {
+            const float4 row = c->ctab[edge_combo(c, S.node)];
+            const float ce = S.comp == 0 ? row.x : S.comp == 1 ? row.y : row.z;
+            if (ce == 0.0f) return fail(FDTD_EINVAL, "a source edge became PEC");
+            S.coef = (double)ce * c->dt / kEps0 / (c->started ? c->h.scale : 1.0);
+        }
+        if (c->started)
+            CK(cudaMemcpyAsync((void *)c->h.src, c->src.data(), sizeof(Source) * c->src.size(), cudaMemcpyHostToDevice,
+                               c->cur));
+    }
+    (void)old;
+    return fdtd_reset(c);
+}
+
+int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
+{
+    if (!c || !info) return fail(FDTD_EINVAL, "NULL argument");
+    CK(cudaStreamSynchronize(c->cur));
+    long long st = 0;
+    CK(cudaMemcpy(&st, c->h.step, sizeof(st), cudaMemcpyDeviceToHost));
+    const Board &h = c->h;
+    info->nx = h.nx; info->ny = h.ny; info->nz = h.nz;
+    info->dt = c->dt;
+    info->step = st;
+    info->n_sources = (int)c->src.size();
+    info->n_probes = (int)c->probe.size();
+    info->n_total_steps = h.n_total;
+    info->n_bins = h.n_bins;
+    info->precision = c->prec;
+    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
+    info->interior_nodes = (Lx > 0 && Ly > 0 && Lz > 0) ? Lx * Ly * Lz : 0;
+    info->fused_upml_nodes = (long long)(c->zaux_n[0] + c->zaux_n[1]);
+    long long sn = 0;
+    for (int s = 0; s < h.n_slab; ++s) sn += h.slab[s].n;
+    info->slab_nodes = sn;
+    info->device_bytes = c->device_bytes;
+    info->n_combo = c->n_combo;
+    return FDTD_OK;
+}
+
+void fdtd_destroy(fdtd_ctx *c)
+{
+    if (!c) return;
+    if (c->batch) fdtd_batch_remove(c->batch, c);
+    if (c->cur) cudaStreamSynchronize(c->cur);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->plan_buf) cudaFree(c->plan_buf);
+    for (cudaEvent_t e : c->events) cudaEventDestroy(e);
+    for (void *p : c->allocs) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+// --------------------------------------------------------------------------- batch
+
+int fdtd_batch_create(void *stream, fdtd_batch **out)
+{
+    if (!out) return fail(FDTD_EINVAL, "out is NULL");
+    fdtd_batch *b = new fdtd_batch();
+    if (stream) {
+        b->stream = (cudaStream_t)stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { delete b; return cuda_fail(e, "cudaStreamCreate"); }
+        b->own_stream = true;
+    }
+    b->grid_cap = device_grid_cap();
+    *out = b;
+    return FDTD_OK;
+}
+
+int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t)
+{
+    if (!b || !t) return fail(FDTD_EINVAL, "NULL argument");
+    fdtd_tuning n = b->tune;
+    if (t->tile_x > 0) n.tile_x = t->tile_x;
+    if (t->tile_y > 0) n.tile_y = t->tile_y;
+    if (t->zseg > 0) n.zseg = t->zseg;
+    if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
+    if (n.tile_x != 32 || (n.tile_y != 2 && n.tile_y != 4 && n.tile_y != 8))
+        return fail(FDTD_EINVAL, "fused tile is 32 x tile_y with tile_y in {2, 4, 8}");
+    b->tune = n;
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c, int n_steps)
+{
+    if (!b || !c) return fail(FDTD_EINVAL, "NULL argument");
+    if (c->batch) return fail(FDTD_EINVAL, "context already in a batch");
+    if (n_steps < 0) return fail(FDTD_EINVAL, "n_steps must be >= 0");
+    if (b->prec >= 0 && !b->members.empty() && c->prec != b->prec)
+        return fail(FDTD_EINVAL, "all boards of a batch must share the precision mode");
+    CK(cudaStreamSynchronize(c->cur));
+    c->cur = b->stream;
+    if (int r = finalize(c)) { c->cur = c->stream; return r; }
+    CK(launch_set_i64(c->h.stop, c->host_step + n_steps, b->stream));
+    c->batch = b;
+    b->members.push_back(c);
+    b->remaining.push_back(n_steps);
+    b->prec = c->prec;
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_batch_remove(fdtd_batch *b, fdtd_ctx *c)
+{
+    if (!b || !c) return fail(FDTD_EINVAL, "NULL argument");
+    auto it = std::find(b->members.begin(), b->members.end(), c);
+    if (it == b->members.end()) return fail(FDTD_EINVAL, "context not in this batch");
+    CK(cudaStreamSynchronize(b->stream));
+    const size_t k = it - b->members.begin();
+    b->members.erase(it);
+    b->remaining.erase(b->remaining.begin() + k);
+    c->batch = nullptr;
+    c->cur = c->stream;
+    CK(launch_set_i64(c->h.stop, LLONG_MAX, c->cur));
+    b->dirty = true;
+    return FDTD_OK;
+}
+
+int fdtd_batch_step(fdtd_batch *b, int n, int *n_done)
+{
+    if (!b) return fail(FDTD_EINVAL, "NULL batch");
+    if (n < 0) return fail(FDTD_EINVAL, "n must be >= 0");
+    long long most = 0;
+    for (long long r : b->remaining) most = std::max(most, r);
+    const int run = (int)std::min<long long>(n, most);
+    if (run > 0 && !b->members.empty()) {
+        if (b->dirty) {
+            std::vector<long long> host;
+            if (int r = build_plan(b->members, b->tune, b->plan_buf, b->plan_cap, b->plan, b->stream, host)) return r;
+            CK(cudaStreamSynchronize(b->stream));
+            if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+            b->dirty = false;
+        }
+        if (int r = run_steps(b->plan, b->prec, b->grid_cap, run, b->tune.graph_chunk, b->graph, b->graph_chunk,
+                              b->stream))
+            return r;
+        for (size_t m = 0; m < b->members.size(); ++m) {
+            const long long did = std::min<long long>(run, b->remaining[m]);
+            b->remaining[m] -= did;
+            b->members[m]->host_step += did;
+        }
+    }
+    if (n_done) {
+        int d = 0;
+        for (long long r : b->remaining) d += (r == 0);
+        *n_done = d;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_batch_remaining(fdtd_batch *b, fdtd_ctx *c, long long *remaining)
+{
+    if (!b || !c || !remaining) return fail(FDTD_EINVAL, "NULL argument");
+    auto it = std::find(b->members.begin(), b->members.end(), c);
+    if (it == b->members.end()) return fail(FDTD_EINVAL, "context not in this batch");
+    *remaining = b->remaining[it - b->members.begin()];
+    return FDTD_OK;
+}
+
+int fdtd_batch_sync(fdtd_batch *b)
+{
+    if (!b) return fail(FDTD_EINVAL, "NULL batch");
+    CK(cudaStreamSynchronize(b->stream));
+    for (fdtd_ctx *c : b->members)
+        if (int r = check_status(c)) return r;
+    return FDTD_OK;
+}
+
+void fdtd_batch_destroy(fdtd_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    for (fdtd_ctx *c : b->members) {
+        c->batch = nullptr;
+        c->cur = c->stream;
+        launch_set_i64(c->h.stop, LLONG_MAX, c->cur);
+    }
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->plan_buf) cudaFree(b->plan_buf);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

