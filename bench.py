@@ -123,6 +123,8 @@ def _workload(name: str, seed_offset: int = 0):
         return W.multilayer_board(seed=3 + seed_offset)
     if name == "multilayer_q":
         return W.multilayer_board(seed=3 + seed_offset, scale=4)
+    if name == "multilayer_h":
+        return W.multilayer_board(seed=3 + seed_offset, scale=2)
     raise ValueError(name)
 
 
@@ -161,6 +163,8 @@ def run_single(args, world, rank, local):
     prob = _workload(args.workload, seed_offset=rank)
     window = args.window
     s = solver.Solver(prob, precision=args.precision)
+    if args.tile_x or args.tile_y or args.zseg:
+        s.set_tuning(tile_x=args.tile_x, tile_y=args.tile_y, zseg=args.zseg)
     inf = s.info()
     cells = prob.cells
     interior_nodes = inf["interior_nodes"]
@@ -247,6 +251,8 @@ def run_single(args, world, rank, local):
                      "bytes_per_unit": bytes_per_node, "units_per_launch": interior_nodes,
                      "upml_aux_bytes_per_launch": 32 * upml_nodes, "algorithmic_bytes_per_launch": alg_bytes,
                      "mean_launch_ms": round(t_int * 1e3, 5)},
+        "tuning": {"tile_x": args.tile_x or "default", "tile_y": args.tile_y or "default",
+                   "zseg": args.zseg or "default"},
         "gpu_launches": int(args.steps * (window * 4 + 2)),
         "clocks": clk.summary(),
         "e2e": e2e,
@@ -306,9 +312,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="multilayer", choices=["small", "realistic", "multilayer", "multilayer_q"])
+    ap.add_argument("--workload", default="multilayer", choices=["small", "realistic", "multilayer", "multilayer_h", "multilayer_q"])
     ap.add_argument("--window", type=int, default=200)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--tile-x", type=int, default=0, help="fused tile width (32, 64, 128); 0 = tuned default")
+    ap.add_argument("--tile-y", type=int, default=0, help="fused tile height (2, 4, 8); 0 = tuned default")
+    ap.add_argument("--zseg", type=int, default=0, help="fused z-segment length; 0 = tuned default")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")

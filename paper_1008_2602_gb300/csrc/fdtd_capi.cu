@@ -8,6 +8,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <array>
@@ -86,7 +87,7 @@ struct fdtd_ctx {
     long long host_step = 0;
     fdtd_batch *batch = nullptr;
     // single-board plan and graph
-    fdtd_tuning tune{32, 4, 16, 16};
+    fdtd_tuning tune{62, 4, 25, 16};
     bool plan_dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;   // device [0]=board ptr, then prefixes
@@ -98,6 +99,8 @@ struct fdtd_ctx {
     int grid_cap = 0;
     std::vector<cudaEvent_t> events; // fdtd_step_profiled
     size_t zaux_n[2] = {0, 0};       // elements per fused-region z-UPML auxiliary array
+    long long zplanes[2] = {0, 0};   // planes of the two z-UPML boxes
+    CUtensorMap *tm_dev = nullptr;   // kNumMaps descriptors in device memory
 };
 
 struct fdtd_batch {
@@ -105,7 +108,7 @@ struct fdtd_batch {
     bool own_stream = false;
     std::vector<fdtd_ctx *> members;
     std::vector<long long> remaining;
-    fdtd_tuning tune{32, 4, 16, 16};
+    fdtd_tuning tune{62, 4, 25, 16};
     bool dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;
@@ -390,11 +393,91 @@ int finalize(fdtd_ctx *c)
     return upload_board(c);
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3D tiled map over a [d2][d1][d0] array of es-byte elements, box b0 x b1 x 1.
+int encode3d(CUtensorMap *m, CUtensorMapDataType dt, int es, const void *base, uint64_t d0, uint64_t d1, uint64_t d2,
+             uint32_t b0, uint32_t b1)
+{
+    PFN_cuTensorMapEncodeTiled_v12000 fn = tmap_encoder();
+    if (!fn) return fail(FDTD_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    if (((uintptr_t)base & 15) || ((d0 * es) & 15) || ((b0 * (uint64_t)es) & 15))
+        return fail(FDTD_EINVAL, "tensor map would break the 16-byte alignment rules");
+    cuuint64_t dims[3] = {d0, d1, d2};
+    cuuint64_t strides[2] = {d0 * es, d0 * d1 * es};
+    cuuint32_t box[3] = {b0, b1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(FDTD_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return FDTD_OK;
+}
+
+// (Re)build the board's TMA descriptors for fused tiles of tx x ty columns.
+int encode_maps(fdtd_ctx *c, int tx, int ty)
+{
+    Board &h = c->h;
+    if (h.tm && h.tm_ty == ty && h.tm_tx == tx) return FDTD_OK;
+    if (h.ix1 <= h.ix0) { h.tm_tx = tx; h.tm_ty = ty; return FDTD_OK; }   // no fused region
+    std::vector<CUtensorMap> maps(kNumMaps);
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * kNumMaps);
+    const CUtensorMapDataType fdt = c->prec == FDTD_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                  : c->prec == FDTD_FP16_STORE ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const int es = elem_size(c->prec);
+    const uint64_t d0 = h.pitch, d1 = h.ny + 1, d2 = h.nz + 1;
+    for (int par = 0; par < 2; ++par)
+        for (int comp = 0; comp < 3; ++comp) {
+            if (int r = encode3d(&maps[tm_e(par, comp)], fdt, es, h.f[par][comp], d0, d1, d2, box_e(tx), ty + 2)) return r;
+            if (int r = encode3d(&maps[tm_h(par, comp)], fdt, es, h.f[par][3 + comp], d0, d1, d2, box_h(tx), ty + 1)) return r;
+        }
+    if (int r = encode3d(&maps[kTmCid], h.id16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                         h.id16 ? 2 : 1, h.cid, d0, d1, d2, h.id16 ? box_c16(tx) : box_c8(tx), ty))
+        return r;
+    const uint64_t Ly = h.iy1 - h.iy0;
+    for (int bx = 0; bx < 2; ++bx) {
+        if (!c->zplanes[bx]) continue;
+        for (int a = 0; a < 2; ++a) {
+            if (int r = encode3d(&maps[tm_zd(bx, a)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zD[bx][a], h.zpitch, Ly,
+                                 c->zplanes[bx], box_a(tx), ty + 1))
+                return r;
+            for (int par = 0; par < 2; ++par)
+                if (int r = encode3d(&maps[tm_zb(bx, a, par)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zB[bx][a][par],
+                                     h.zpitch, Ly, c->zplanes[bx], box_a(tx), ty + 1))
+                    return r;
+        }
+    }
+    // a fresh buffer per encoding: a descriptor address is never rewritten
+    // while a kernel may still hold it in its descriptor cache
+    if (int r = dalloc(c, &c->tm_dev, sizeof(CUtensorMap) * kNumMaps)) return r;
+    CK(cudaMemcpyAsync(c->tm_dev, maps.data(), sizeof(CUtensorMap) * kNumMaps, cudaMemcpyHostToDevice, c->cur));
+    CK(cudaStreamSynchronize(c->cur));
+    h.tm = c->tm_dev;
+    h.tm_tx = tx;
+    h.tm_ty = ty;
+    return upload_board(c);
+}
+
 long long interior_items(const Board &h, const fdtd_tuning &t)
 {
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
     if (Lx <= 0 || Ly <= 0 || Lz <= 0) return 0;
-    return ((Lx + 31) / 32) * ((Ly + t.tile_y - 1) / t.tile_y) * ((Lz + t.zseg - 1) / t.zseg);
+    return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * ((Lz + t.zseg - 1) / t.zseg);
 }
 
 long long dft_items(const Board &h)
@@ -408,7 +491,7 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
                Plan &plan, cudaStream_t st, std::vector<long long> &host)
 {
     const int nb = (int)boards.size();
-    const size_t words = (size_t)nb + 3 * ((size_t)nb + 1);
+    const size_t words = (size_t)nb + 3 * ((size_t)nb + 1) + 1;   // + work counter
     host.assign(words, 0);
     long long *ptrs = host.data();
     long long *ip = ptrs + nb, *sp = ip + nb + 1, *dp = sp + nb + 1;
@@ -441,6 +524,7 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.n_int = ip[nb];
     plan.n_slab = sp[nb];
     plan.n_dft = dp[nb];
+    plan.work = (int *)(buf + nb + 3 * (nb + 1));
     return FDTD_OK;
 }
 
@@ -481,6 +565,7 @@ int check_status(fdtd_ctx *c)
 {
     int st = 0;
     CK(cudaMemcpy(&st, c->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 2) return fail(FDTD_ETIMEOUT, "a fused-kernel TMA wait gave up (results of this run are invalid)");
     if (st & 1) return fail(FDTD_EUNSTABLE, "non-finite probe sample (unstable run: check the Courant number)");
     return FDTD_OK;
 }
@@ -504,6 +589,8 @@ int set_geometry(fdtd_ctx *c, const uint8_t *mat)
         c->h.cid = d;
         c->h.ctab = t;
         c->h.id16 = id16;
+        c->h.tm_ty = 0;   // the id tensor map must be rebuilt
+        c->h.tm_tx = 0;
         c->plan_dirty = true;
     }
     if (id16) {
@@ -601,6 +688,12 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
                          : grid->courant / (kC0 * std::sqrt(1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dy * grid->dy) +
                                                              1.0 / (grid->dz * grid->dz)));
     c->grid_cap = device_grid_cap();
+    static bool smem_limits = false;
+    if (!smem_limits) {
+        cudaError_t e = fused_set_smem_limits();
+        if (e != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ECUDA, std::string("fused kernel shared memory: ") + cudaGetErrorString(e)); }
+        smem_limits = true;
+    }
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -626,11 +719,13 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
 
     int r = FDTD_OK;
     const size_t fbytes = (size_t)h.nodes * elem_size(precision);
-    for (int p = 0; p < 2 && !r; ++p)
-        for (int f = 0; f < 6 && !r; ++f) {
-            r = dalloc(c, &h.f[p][f], fbytes);
-            if (!r) { cudaError_t e = cudaMemsetAsync(h.f[p][f], 0, fbytes, c->cur); if (e) r = cuda_fail(e, "memset"); }
-        }
+    // the six components of one parity are contiguous (component stride = nodes)
+    for (int p = 0; p < 2 && !r; ++p) {
+        unsigned char *blk = nullptr;
+        r = dalloc(c, &blk, 6 * fbytes);
+        if (!r) { cudaError_t e = cudaMemsetAsync(blk, 0, 6 * fbytes, c->cur); if (e) r = cuda_fail(e, "memset"); }
+        for (int f = 0; f < 6 && !r; ++f) h.f[p][f] = blk + f * fbytes;
+    }
     h.cid = nullptr;
     h.ctab = nullptr;
     h.id16 = -1;
@@ -714,7 +809,9 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         if (!fused) continue;
         const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
         if (planes <= 0) continue;
-        const size_t n = (size_t)planes * (h.ix1 - h.ix0) * (h.iy1 - h.iy0);
+        h.zpitch = ((h.ix1 - h.ix0) + 7) & ~7;
+        const size_t n = (size_t)planes * h.zpitch * (h.iy1 - h.iy0);
+        c->zplanes[bx] = planes;
         for (int a = 0; a < 2 && !r; ++a) {
             float *ptr[3] = {nullptr, nullptr, nullptr};
             for (int t = 0; t < 3 && !r; ++t) {
@@ -808,8 +905,8 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t)
     if (t->tile_y > 0) n.tile_y = t->tile_y;
     if (t->zseg > 0) n.zseg = t->zseg;
     if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
-    if (n.tile_x != 32 || (n.tile_y != 2 && n.tile_y != 4 && n.tile_y != 8))
-        return fail(FDTD_EINVAL, "fused tile is 32 x tile_y with tile_y in {2, 4, 8}");
+    if (!fused_tile_supported(n.tile_x, n.tile_y))
+        return fail(FDTD_EINVAL, "fused tile (tile_x x tile_y) must be 62x4, 62x8, 124x4 or 124x8");
     c->tune = n;
     c->plan_dirty = true;
     return FDTD_OK;
@@ -832,6 +929,7 @@ int fdtd_step(fdtd_ctx *c, int n)
 static int prepare_single(fdtd_ctx *c)
 {
     if (int r = finalize(c)) return r;
+    if (int r = encode_maps(c, c->tune.tile_x, c->tune.tile_y)) return r;
     if (c->plan_dirty) {
         std::vector<long long> host;
         std::vector<fdtd_ctx *> one{c};
@@ -1069,8 +1167,8 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t)
     if (t->tile_y > 0) n.tile_y = t->tile_y;
     if (t->zseg > 0) n.zseg = t->zseg;
     if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
-    if (n.tile_x != 32 || (n.tile_y != 2 && n.tile_y != 4 && n.tile_y != 8))
-        return fail(FDTD_EINVAL, "fused tile is 32 x tile_y with tile_y in {2, 4, 8}");
+    if (!fused_tile_supported(n.tile_x, n.tile_y))
+        return fail(FDTD_EINVAL, "fused tile (tile_x x tile_y) must be 62x4, 62x8, 124x4 or 124x8");
     b->tune = n;
     b->dirty = true;
     return FDTD_OK;
@@ -1120,6 +1218,8 @@ int fdtd_batch_step(fdtd_batch *b, int n, int *n_done)
     const int run = (int)std::min<long long>(n, most);
     if (run > 0 && !b->members.empty()) {
         if (b->dirty) {
+            for (fdtd_ctx *m : b->members)
+                if (int r = encode_maps(m, b->tune.tile_x, b->tune.tile_y)) return r;
             std::vector<long long> host;
             if (int r = build_plan(b->members, b->tune, b->plan_buf, b->plan_cap, b->plan, b->stream, host)) return r;
             CK(cudaStreamSynchronize(b->stream));

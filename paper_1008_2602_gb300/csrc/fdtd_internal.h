@@ -31,6 +31,7 @@
 // for components whose recurrence there is not trivial.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -89,9 +90,13 @@ struct Board {
     int wall[6];
     int depth[6];                 // UPML cells per face
     int ix0, ix1, iy0, iy1, iz0, iz1;   // fused xy box; non-UPML z range [iz0, iz1)
-    // z-UPML boxes of the fused region: [0] k in [1, iz0), [1] k in [iz1, nz)
+    // z-UPML boxes of the fused region: [0] k in [1, iz0), [1] k in [iz1, nz);
+    // element (i, j, k) at ((k - k0) * (iy1 - iy0) + j - iy0) * zpitch + i - ix0
     float *zD[2][2];              // [box][y, z]         D~y, D~z
     float *zB[2][2][2];           // [box][y, z][parity] B~y, B~z
+    int zpitch;                   // row pitch of the z-UPML boxes (multiple of 8)
+    int tm_tx, tm_ty;             // tile shape the tensor maps were encoded for
+    const CUtensorMap *tm;        // kNumMaps TMA descriptors (see tm_* below)
     int n_slab;
     int slab_blocks;              // slab-kernel blocks for this board
     Slab slab[kMaxSlab];
@@ -120,7 +125,23 @@ struct Plan {
     const long long *slab_prefix; // [nb + 1] slab blocks
     const long long *dft_prefix;  // [nb + 1] DFT warps
     long long n_int, n_slab, n_dft;
+    int *work;                    // fused-kernel work counter (zeroed before every launch)
 };
+
+// TMA descriptor slots of a board (3D maps: x, y, plane).
+__host__ __device__ constexpr int tm_e(int par, int c) { return par * 3 + c; }               // E box  48 x (TY+2)
+__host__ __device__ constexpr int tm_h(int par, int c) { return 6 + par * 3 + c; }           // H box  40 x (TY+1)
+constexpr int kTmCid = 12;                                                // ids    48|40 x TY
+__host__ __device__ constexpr int tm_zd(int box, int a) { return 13 + box * 2 + a; }         // D~     40 x (TY+1)
+__host__ __device__ constexpr int tm_zb(int box, int a, int par) { return 17 + (box * 2 + a) * 2 + par; }   // B~
+constexpr int kNumMaps = 25;
+// TMA box widths for a tile of tx columns (x rounded down to 16 bytes)
+__host__ __device__ constexpr int box_up(int x, int m) { return (x + m - 1) / m * m; }
+__host__ __device__ constexpr int box_e(int tx) { return box_up(tx + 9, 8); }
+__host__ __device__ constexpr int box_h(int tx) { return box_up(tx + 8, 8); }
+__host__ __device__ constexpr int box_c8(int tx) { return box_up(tx + 15, 16); }
+__host__ __device__ constexpr int box_c16(int tx) { return box_up(tx + 7, 8); }
+__host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 4, 4); }
 
 constexpr int kSlabThreads = 256;
 constexpr int kDftProbeGroup = 4;
@@ -135,5 +156,7 @@ cudaError_t launch_set_i64(long long *p, long long v, cudaStream_t st);
 cudaError_t launch_energy(const Board *b_dev, const Board &b_host, double *partials, int n_part,
                           double *out2, cudaStream_t st);
 int energy_partials(const Board &b_host);
+bool fused_tile_supported(int tile_x, int tile_y);
+cudaError_t fused_set_smem_limits();
 
 }  // namespace fdtd

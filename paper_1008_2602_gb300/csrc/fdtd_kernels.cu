@@ -22,6 +22,8 @@
 
 namespace fdtd {
 
+
+
 // ------------------------------------------------------------------ storage
 template <typename T>
 struct Io;
@@ -121,7 +123,7 @@ __device__ __forceinline__ int zbox_of(const Board *B, int k) { return k < B->iz
 __device__ __forceinline__ long long zaux_index(const Board *B, int box, int i, int j, int k)
 {
     const int k0 = box == 1 ? 1 : B->iz1;
-    return ((long long)(k - k0) * (B->iy1 - B->iy0) + (j - B->iy0)) * (long long)(B->ix1 - B->ix0) + (i - B->ix0);
+    return ((long long)(k - k0) * (B->iy1 - B->iy0) + (j - B->iy0)) * (long long)B->zpitch + (i - B->ix0);
 }
 
 // New H~x, H~y, H~z at a fused-region node from already-fetched operands.
@@ -148,245 +150,403 @@ __device__ __forceinline__ float fused_hz(float h, float sc, int zb, const ZCoef
     return upml_h2(h, sc, kOne, kOne, z.zi, true, Bo, Bn);
 }
 
-// Tiled fused H+E kernel over the fused region.  A CTA owns a 32 x TY tile of
-// (i, j) columns and marches a z-segment.  Per plane k it keeps E^n of planes
-// k and k+1 (tile plus one-node halo) in shared memory, computes H~^{n+1/2}(k)
-// for the tile plus the low-x column and low-y row it needs (recomputed from
-// the same inputs when they lie in the fused region, read from the slab
-// kernel's output otherwise), then E^{n+1}(k) for the tile.  E^n of plane k+2
-// and the tile's H~^{n-1/2}(k+1) are prefetched into registers while plane k
-// is computed.
-template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY, 512 / (32 * TY)) k_fused(Plan plan)
+// ------------------------------------------------------------------ TMA + mbarrier
+__device__ __forceinline__ uint32_t s_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, uint32_t n)
 {
-    constexpr int NT = 32 * TY;
-    constexpr int EW = 34, EH = TY + 2, EPL = EW * EH;
-    constexpr int NE = (3 * EPL + NT - 1) / NT;
-    constexpr int HW = 33, HH = TY + 1;
-    constexpr int HCW = TY > 1 ? 1 : 0;          // warp computing the low-x halo column
-    __shared__ float sE[3][3][EH][EW];
-    __shared__ float sH[3][HH][HW];
-    const int lx = threadIdx.x, ly = threadIdx.y, tid = ly * 32 + lx;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_addr(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(s_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait on a phase: gives up after ~2^21 polls (each poll itself
+// suspends for a hardware-defined slice) and reports it in *status.
+__device__ __forceinline__ void mbar_wait(uint64_t *b, uint32_t parity, int *status, int *abort_flag)
+{
+    if (*(volatile int *)abort_flag) return;
+    for (uint32_t it = 0; it < (1u << 21); ++it)
+        if (mbar_try(b, parity)) return;
+    atomicOr(status, 2);
+    *(volatile int *)abort_flag = 1;
+}
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+            s_addr(dst)),
+        "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(s_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-    for (long long item = blockIdx.x; item < plan.n_int; item += gridDim.x) {
-        const int b = find_board(plan.int_prefix, plan.nb, item);
-        const Board *__restrict__ B = plan.boards[b];
-        if (!board_active(B)) continue;
-        const long long step = *((volatile long long *)B->step);
-        const int par = (int)(step & 1);
-        const long long local = item - __ldg(plan.int_prefix + b);
-        const int nx = B->nx, ny = B->ny, nz = B->nz;
-        const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1;
-        const int ntx = (ix1 - ix0 + 31) / 32, nty = (iy1 - iy0 + TY - 1) / TY;
-        const int tx = (int)(local % ntx);
-        const long long rest = local / ntx;
-        const int ty = (int)(rest % nty), tz = (int)(rest / nty);
-        const int i0 = ix0 + tx * 32, j0 = iy0 + ty * TY;
-        const int kb = 1 + tz * plan.zseg, ke = min(kb + plan.zseg, nz);
-        const int i = i0 + lx, j = j0 + ly;
-        const bool own = i < ix1 && j < iy1;
+template <typename T>
+__device__ __forceinline__ float cvt(T v);
+template <>
+__device__ __forceinline__ float cvt<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float cvt<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+// Shared-memory stage of one plane for a tile of W warps x 31 columns by TY
+// rows.  Boxes start at x rounded down to the 16-byte TMA boundary:
+//   E  3 x (TY+2) x EW   nodes i0-1 .. i0+31W, rows j0-1 .. j0+TY
+//   H  3 x (TY+1) x HW   nodes i0-1 .. i0+31W-1, rows j0-1 .. j0+TY-1
+//   id TY x C8W bytes (or TY x C16W uint16), rows j0 .. j0+TY-1
+// Every box starts 128-byte aligned.
+template <typename T, int TY, int W>
+struct Stage {
+    static constexpr int al(int x) { return (x + 127) & ~127; }
+    static constexpr int TX = 31 * W;
+    static constexpr int ES = (int)sizeof(T);
+    static constexpr int EW = box_e(TX), HW = box_h(TX), C8W = box_c8(TX), C16W = box_c16(TX);
+    static constexpr int E_COMP = (TY + 2) * EW, H_COMP = (TY + 1) * HW;
+    static constexpr int E_CS = al(E_COMP * ES) / ES, H_CS = al(H_COMP * ES) / ES;
+    static constexpr int E_BYTES = 3 * E_COMP * ES;
+    static constexpr int H_BYTES = 3 * H_COMP * ES;
+    static constexpr int C8_BYTES = TY * C8W, C16_BYTES = TY * C16W * 2;
+    static constexpr int E_OFF = 0;
+    static constexpr int H_OFF = 3 * E_CS * ES;
+    static constexpr int C_OFF = H_OFF + 3 * H_CS * ES;
+    static constexpr int ITEM_OFF = C_OFF + al(C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES);   // item id of the plane
+    static constexpr int BYTES = ITEM_OFF + 128;
+};
+
+template <typename T, int TY, int W, int NS>
+struct FusedLayout {
+    using St = Stage<T, TY, W>;
+    static constexpr int BAR_OFF = NS * St::BYTES;
+    static constexpr int BYTES = BAR_OFF + 2 * NS * 8 + 16;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *b)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_addr(b)) : "memory");
+}
+
+// Work item -> tile; identical in the producer and the consumer warps.
+struct Tile {
+    const Board *B;
+    int ok;
+    int i0, j0, kb, ke, kstart, par;
+};
+
+template <int TY, int W>
+__device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
+{
+    Tile t;
+    const int b = find_board(plan.int_prefix, plan.nb, item);
+    t.B = plan.boards[b];
+    t.ok = board_active(t.B);
+    const long long step = *((volatile long long *)t.B->step);
+    t.par = (int)(step & 1);
+    const long long local = item - __ldg(plan.int_prefix + b);
+    const int ntx = (t.B->ix1 - t.B->ix0 + 31 * W - 1) / (31 * W), nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
+    const int tx = (int)(local % ntx);
+    const long long rest = local / ntx;
+    const int ty = (int)(rest % nty), tz = (int)(rest / nty);
+    t.i0 = t.B->ix0 + tx * 31 * W;
+    t.j0 = t.B->iy0 + ty * TY;
+    t.kb = 1 + tz * plan.zseg;
+    t.ke = min(t.kb + plan.zseg, t.B->nz);
+    t.kstart = t.kb >= 2 ? t.kb - 1 : t.kb;
+    return t;
+}
+
+// Fused H+E kernel over the fused region, fed by TMA, warp-specialised.
+// Warps 0..W-1 compute; warp W (one lane) is the producer, streaming planes
+// kstart..ke of the tile into an NS-stage ring (E^n with a one-node halo,
+// H~^{n-1/2} with the low halo row and column, coefficient ids), each stage
+// with a "full" mbarrier (TMA bytes) and an "empty" one (one arrival per
+// compute warp).  Compute warp w owns a strip of 31 columns: lane l sits on
+// column i0-1+31w+l, lane 0 being the strip's low-x halo.  Per plane k a lane
+// marches the tile's rows in y: it forms H~^{n+1/2}(k) at its column for the
+// halo row j0-1 and then row by row, so H(j-1) is already in registers, takes
+// H(i-1) from the lane to its left with a shuffle, and updates E^{n+1}(k).
+// H~ of halo nodes outside the fused region is read from the slab kernel's
+// output instead.  The plane below the segment is run once for the tile's
+// H~x, H~y there; the plane above is read for E only.  In z-UPML planes
+// (sigma_z only) H~y, H~z carry B~y, B~z and E_y, E_z carry D~y, D~z.
+template <typename T, int TY, int W, int NS>
+__global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan)
+{
+    using St = Stage<T, TY, W>;
+    using L = FusedLayout<T, TY, W, NS>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
+    uint64_t *empty = full + NS;
+    int *abort_flag = reinterpret_cast<int *>(empty + NS);
+    const int lx = threadIdx.x, wy = threadIdx.y;
+
+    if (wy == 0 && lx == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], W);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (wy == W) {
+        // ------------------------------------------------------------ producer
+        // Items are taken from a global counter; the first plane of an item
+        // carries the item id to the compute warps, an id of -1 ends the work.
+        if (lx != 0) return;
+        uint32_t eph = 0;
+        long long q = 0;
+        int s = 0;
+        auto acquire = [&]() {
+            if (q >= NS) {
+                mbar_wait(&empty[s], (eph >> s) & 1u, plan.boards[0]->status, abort_flag);
+                eph ^= 1u << s;
+            }
+        };
+        for (;;) {
+            const long long item = atomicAdd(plan.work, 1);
+            if (item >= plan.n_int) break;
+            const Tile t = decode_tile<TY, W>(plan, item);
+            const Board *B = t.B;
+            const CUtensorMap *tm = B->tm;
+            const int id16 = B->id16;
+            const int xe0 = (t.i0 - 1) & ~7;
+            const int xc0 = id16 ? (t.i0 & ~7) : (t.i0 & ~15);
+            const int last = t.ok ? t.ke : t.kstart;    // inactive board: one empty plane
+            for (int p = t.kstart; p <= last; ++p, ++q, s = (s + 1 == NS ? 0 : s + 1)) {
+                acquire();
+                unsigned char *st = smem + s * St::BYTES;
+                *reinterpret_cast<volatile long long *>(st + St::ITEM_OFF) = (p == t.kstart) ? item : -2;
+                if (!t.ok) {
+                    mbar_expect_tx(&full[s], 0);
+                    continue;
+                }
+                const bool e_only = (p == t.ke);
+                uint32_t bytes = St::E_BYTES;
+                if (!e_only) bytes += St::H_BYTES + (id16 ? St::C16_BYTES : St::C8_BYTES);
+                mbar_expect_tx(&full[s], bytes);
+                for (int c = 0; c < 3; ++c)
+                    tma_load_3d(st + St::E_OFF + c * St::E_CS * St::ES, tm + tm_e(t.par, c), xe0, t.j0 - 1, p, &full[s]);
+                if (!e_only) {
+                    for (int c = 0; c < 3; ++c)
+                        tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tm_h(t.par, c), xe0, t.j0 - 1, p,
+                                    &full[s]);
+                    tma_load_3d(st + St::C_OFF, tm + kTmCid, xc0, t.j0, p, &full[s]);
+                }
+            }
+        }
+        acquire();
+        *reinterpret_cast<volatile long long *>(smem + s * St::BYTES + St::ITEM_OFF) = -1;
+        mbar_expect_tx(&full[s], 0);
+        return;
+    }
+
+    // ---------------------------------------------------------------- compute warps
+    uint32_t fph = 0;
+    int sq = 0;
+    for (;;) {
+        mbar_wait(&full[sq], (fph >> sq) & 1u, plan.boards[0]->status, abort_flag);
+        const long long item = *reinterpret_cast<volatile long long *>(smem + sq * St::BYTES + St::ITEM_OFF);
+        if (item < 0) break;   // -1: no more work (the stage is left full)
+        const Tile t = decode_tile<TY, W>(plan, item);
+        if (!t.ok) {           // one empty plane was sent for an inactive board
+            fph ^= 1u << sq;
+            __syncwarp();
+            if (lx == 0) mbar_arrive(&empty[sq]);
+            sq = sq + 1 == NS ? 0 : sq + 1;
+            continue;
+        }
+        const Board *__restrict__ B = t.B;
+        const int par = t.par, i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke, kstart = t.kstart;
+        const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0, iz1 = B->iz1;
         const int X = B->pitch;
-        const long long P = B->plane;
+        const long long P = B->plane, NN = B->nodes;
         const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
-        const Fields<T> F(B, par);
-        const Coef *__restrict__ czi = B->cw[2][0];
-        const Coef *__restrict__ czh = B->cw[2][1];
-
-        // halo duties: row (i, j0-1) by warp 0, column (i0-1, j0+lx) by warp HCW lanes < TY
-        const bool row_duty = (ly == 0) && (i < ix1);
-        const bool row_calc = row_duty && (j0 - 1 >= iy0);
-        const bool col_duty = (ly == HCW) && (lx < TY) && (j0 + lx < iy1);
-        const bool col_calc = col_duty && (i0 - 1 >= ix0);
-        const int cj = j0 + lx;                          // column-halo node (i0-1, cj)
-
-        auto load_plane = [&](int kp, float (&r)[NE]) {
+        const int id16 = B->id16;
+        const float4 *__restrict__ ctab = B->ctab;
+        int *const status = B->status;
+        const int c = i0 - 1 + 31 * wy + lx;                  // this lane's column
+        const bool own_col = (lx > 0) && (c < ix1);
+        const bool col_slab = (c < ix0);                      // only lane 0 of warp 0 can be outside
+        const bool row_slab = (j0 - 1 < iy0);
+        const int ecol = ((i0 - 1) & 7) + 31 * wy + lx;       // column in the E/H boxes
+        const int ccol = (i0 - (id16 ? (i0 & ~7) : (i0 & ~15))) - 1 + 31 * wy + lx;   // in the id box
+        // global element (c, j0-1, kstart) in the output parity, advanced by P per plane
+        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(j0 - 1) * X + c);
+        const int zrow = B->zpitch;
+        const long long zplane = (long long)(iy1 - iy0) * zrow;
+        const long long zcol = (long long)(j0 - 1 - iy0) * zrow + (c - ix0);   // aux of (c, j0-1)
+        int s0 = sq, s1 = sq + 1 == NS ? 0 : sq + 1;
+        // z-UPML auxiliaries of this lane's column, fetched one plane ahead:
+        // B~y, B~z for box rows 0..TY (halo row and the tile rows), D~y, D~z
+        // for the tile rows
+        struct Aux {
+            float by[TY + 1], bz[TY + 1], dy[TY], dz[TY];
+        };
+        auto fetch_aux = [&](int k, Aux &a) {
+            const int zb = k < iz0 ? 1 : (k >= iz1 ? 2 : 0);
+            if (!zb) return;
+            const long long base = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
+            const float *by = B->zB[zb - 1][0][par], *bz = B->zB[zb - 1][1][par];
+            const float *dy = B->zD[zb - 1][0], *dz = B->zD[zb - 1][1];
+            const bool cin = !col_slab && c < ix1;
 #pragma unroll
-            for (int u = 0; u < NE; ++u) {
-                const int f = tid + u * NT;
-                float v = 0.f;
-                if (f < 3 * EPL) {
-                    const int c = f / EPL, rr = f - c * EPL, sy = rr / EW, sx = rr - sy * EW;
-                    const int gi = i0 - 1 + sx, gj = j0 - 1 + sy;
-                    if (gi <= nx && gj <= ny && kp <= nz) {
-                        const T *src = c == 0 ? F.ex : (c == 1 ? F.ey : F.ez);
-                        v = Io<T>::ld(src + ((unsigned)kp * (unsigned)P + (unsigned)(gj * X + gi)));
-                    }
+            for (int rr = 0; rr <= TY; ++rr) {
+                const int j = j0 - 1 + rr;
+                if (cin && j >= iy0 && j < iy1) {
+                    const long long x = base + (long long)rr * zrow;
+                    a.by[rr] = __ldg(by + x);
+                    a.bz[rr] = __ldg(bz + x);
+                    if (rr > 0 && lx > 0) { a.dy[rr - 1] = dy[x]; a.dz[rr - 1] = dz[x]; }
                 }
-                r[u] = v;
             }
         };
-        auto store_plane = [&](int stg, const float (&r)[NE]) {
+        Aux ax, axn;
+        fetch_aux(kstart, ax);
+
+        float hk1x[TY], hk1y[TY];   // H~x, H~y of the previous plane, per row
 #pragma unroll
-            for (int u = 0; u < NE; ++u) {
-                const int f = tid + u * NT;
-                if (f < 3 * EPL) {
-                    const int c = f / EPL, rr = f - c * EPL, sy = rr / EW, sx = rr - sy * EW;
-                    sE[stg][c][sy][sx] = r[u];
+        for (int r = 0; r < TY; ++r) { hk1x[r] = 0.f; hk1y[r] = 0.f; }
+        if (kstart == kb) {        // plane kb-1 is an outer z plane: read its H~
+#pragma unroll
+            for (int r = 0; r < TY; ++r)
+                if (own_col && j0 + r < iy1) {
+                    const T *g = gp - P + (long long)(r + 1) * X;
+                    hk1x[r] = Io<T>::ld(g + 3 * NN);
+                    hk1y[r] = Io<T>::ld(g + 4 * NN);
                 }
-            }
-        };
-
-        // per-plane operands of this thread (current and prefetched next plane)
-        struct Ops {
-            float hx, hy, hz;        // own H~^{n-1/2}
-            float rhx, rhz;          // row halo H~ (old, or new if not recomputed)
-            float chy, chz;          // column halo H~
-            float dy, dz, by, bz;    // own auxiliaries (z-UPML planes)
-            float rbz, cby, cbz;     // halo auxiliaries
-            int cid;
-        };
-        auto fetch = [&](int k, Ops &o) {
-            const int zb = zbox_of(B, k);
-            const long long q = (long long)k * P + (long long)j * X + i;
-            if (own) {
-                o.hx = Io<T>::ld(F.hx + q); o.hy = Io<T>::ld(F.hy + q); o.hz = Io<T>::ld(F.hz + q);
-                o.cid = cid_at(B, q);
-                if (zb) {
-                    const long long a = zaux_index(B, zb, i, j, k);
-                    o.dy = B->zD[zb - 1][0][a]; o.dz = B->zD[zb - 1][1][a];
-                    o.by = __ldg(B->zB[zb - 1][0][par] + a); o.bz = __ldg(B->zB[zb - 1][1][par] + a);
-                }
-            }
-            if (row_duty) {
-                const long long r = (long long)k * P + (long long)(j0 - 1) * X + i;
-                if (row_calc) {
-                    o.rhx = Io<T>::ld(F.hx + r); o.rhz = Io<T>::ld(F.hz + r);
-                    if (zb) o.rbz = __ldg(B->zB[zb - 1][1][par] + zaux_index(B, zb, i, j0 - 1, k));
-                } else {
-                    o.rhx = Io<T>::ld(F.ohx + r); o.rhz = Io<T>::ld(F.ohz + r);
-                }
-            }
-            if (col_duty) {
-                const long long r = (long long)k * P + (long long)cj * X + (i0 - 1);
-                if (col_calc) {
-                    o.chy = Io<T>::ld(F.hy + r); o.chz = Io<T>::ld(F.hz + r);
-                    if (zb) {
-                        const long long a = zaux_index(B, zb, i0 - 1, cj, k);
-                        o.cby = __ldg(B->zB[zb - 1][0][par] + a); o.cbz = __ldg(B->zB[zb - 1][1][par] + a);
-                    }
-                } else {
-                    o.chy = Io<T>::ld(F.ohy + r); o.chz = Io<T>::ld(F.ohz + r);
-                }
-            }
-        };
-
-        // own H~x, H~y at plane kb-1 (needed by E(kb))
-        float hxm = 0.f, hym = 0.f;
-        if (own) {
-            const long long q = (long long)(kb - 1) * P + (long long)j * X + i;
-            if (kb - 1 >= 1) {
-                const int zb = zbox_of(B, kb - 1);
-                ZCoef z;
-                z.zi = czi[kb - 1]; z.zh = czh[kb - 1];
-                const float scx = curl2(Io<T>::ld(F.ez + q + X), Io<T>::ld(F.ez + q), Io<T>::ld(F.ey + q + P),
-                                        Io<T>::ld(F.ey + q), Sy, Sz);
-                const float scy = curl2(Io<T>::ld(F.ex + q + P), Io<T>::ld(F.ex + q), Io<T>::ld(F.ez + q + 1),
-                                        Io<T>::ld(F.ez + q), Sz, Sx);
-                float Bo = 0.f, Bn;
-                if (zb) Bo = __ldg(B->zB[zb - 1][0][par] + zaux_index(B, zb, i, j, kb - 1));
-                hxm = fused_hx(Io<T>::ld(F.hx + q), scx, zb, z);
-                hym = fused_hy(Io<T>::ld(F.hy + q), scy, zb, z, Bo, Bn);
-            } else {
-                hxm = Io<T>::ld(F.ohx + q);
-                hym = Io<T>::ld(F.ohy + q);
-            }
         }
-        {
-            float r[NE];
-            load_plane(kb, r);
-            store_plane(kb % 3, r);
-            load_plane(kb + 1, r);
-            store_plane((kb + 1) % 3, r);
-        }
-        Ops cur, nxt;
-        fetch(kb, cur);
-        __syncthreads();
-
-        for (int k = kb; k < ke; ++k) {
-            const int s0 = k % 3, s1 = (k + 1) % 3, s2 = (k + 2) % 3;
-            const bool more = (k + 1 < ke);
-            float rE[NE];
-            if (more) {
-                load_plane(k + 2, rE);
-                fetch(k + 1, nxt);
-            }
-            const int zb = zbox_of(B, k);
+        fph ^= 1u << s0;     // the item's first plane was waited for above
+        (void)status;
+        for (int k = kstart; k < ke; ++k, gp += P) {
+            if (k + 1 < ke) fetch_aux(k + 1, axn);
+            mbar_wait(&full[s1], (fph >> s1) & 1u, status, abort_flag);
+            fph ^= 1u << s1;
+            const unsigned char *st0 = smem + s0 * St::BYTES, *st1 = smem + s1 * St::BYTES;
+            const T *E0 = reinterpret_cast<const T *>(st0 + St::E_OFF) + ecol;
+            const T *E1 = reinterpret_cast<const T *>(st1 + St::E_OFF) + ecol;
+            const T *H0 = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol;
+            const unsigned char *C0 = st0 + St::C_OFF;
+            constexpr int EW = St::EW, HW = St::HW, ECS = St::E_CS, HCS = St::H_CS;
+            const int zb = k < iz0 ? 1 : (k >= iz1 ? 2 : 0);
             ZCoef z;
-            if (zb) { z.zi = czi[k]; z.zh = czh[k]; }
-            const int sx = lx + 1, sy = ly + 1;
-            float hxv = 0.f, hyv = 0.f, hzv = 0.f, nby = 0.f, nbz = 0.f;
-            if (own) {
-                const float scx = curl2(sE[s0][2][sy + 1][sx], sE[s0][2][sy][sx], sE[s1][1][sy][sx], sE[s0][1][sy][sx], Sy, Sz);
-                const float scy = curl2(sE[s1][0][sy][sx], sE[s0][0][sy][sx], sE[s0][2][sy][sx + 1], sE[s0][2][sy][sx], Sz, Sx);
-                const float scz = curl2(sE[s0][1][sy][sx + 1], sE[s0][1][sy][sx], sE[s0][0][sy + 1][sx], sE[s0][0][sy][sx], Sx, Sy);
-                hxv = fused_hx(cur.hx, scx, zb, z);
-                hyv = fused_hy(cur.hy, scy, zb, z, cur.by, nby);
-                hzv = fused_hz(cur.hz, scz, zb, z, cur.bz, nbz);
-                sH[0][sy][sx] = hxv; sH[1][sy][sx] = hyv; sH[2][sy][sx] = hzv;
+            float *zdy = nullptr, *zdz = nullptr, *nzby = nullptr, *nzbz = nullptr;
+            long long za = 0;
+            if (zb) {
+                z.zi = B->cw[2][0][k];
+                z.zh = B->cw[2][1][k];
+                za = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
+                nzby = B->zB[zb - 1][0][par ^ 1]; nzbz = B->zB[zb - 1][1][par ^ 1];
+                zdy = B->zD[zb - 1][0]; zdz = B->zD[zb - 1][1];
             }
-            if (row_duty) {   // node (i, j0-1): smem row sy = 0
-                if (row_calc) {
-                    const float scx = curl2(sE[s0][2][1][sx], sE[s0][2][0][sx], sE[s1][1][0][sx], sE[s0][1][0][sx], Sy, Sz);
-                    const float scz = curl2(sE[s0][1][0][sx + 1], sE[s0][1][0][sx], sE[s0][0][1][sx], sE[s0][0][0][sx], Sx, Sy);
-                    float d;
-                    sH[0][0][sx] = fused_hx(cur.rhx, scx, zb, z);
-                    sH[2][0][sx] = fused_hz(cur.rhz, scz, zb, z, cur.rbz, d);
-                } else {
-                    sH[0][0][sx] = cur.rhx;
-                    sH[2][0][sx] = cur.rhz;
+            const bool full_plane = k >= kb;
+            // H~^{n+1/2}(k) at (c, j0-1+rr) from box row rr; Bo/Bn: B~y, B~z
+            auto hnode = [&](int rr, bool in_f, float &hx, float &hy, float &hz, float &nby, float &nbz) {
+                const float ezr = cvt<T>(E0[2 * ECS + rr * EW]), ezu = cvt<T>(E0[2 * ECS + (rr + 1) * EW]);
+                const float eyr = cvt<T>(E0[ECS + rr * EW]), eyk = cvt<T>(E1[ECS + rr * EW]);
+                const float exr = cvt<T>(E0[rr * EW]), exk = cvt<T>(E1[rr * EW]), exu = cvt<T>(E0[(rr + 1) * EW]);
+                const float ezx = cvt<T>(E0[2 * ECS + rr * EW + 1]), eyx = cvt<T>(E0[ECS + rr * EW + 1]);
+                const float scx = curl2(ezu, ezr, eyk, eyr, Sy, Sz);
+                const float scy = curl2(exk, exr, ezx, ezr, Sz, Sx);
+                const float scz = curl2(eyx, eyr, exu, exr, Sx, Sy);
+                const float Boy = (zb && in_f) ? ax.by[rr] : 0.f;
+                const float Boz = (zb && in_f) ? ax.bz[rr] : 0.f;
+                hx = fused_hx(cvt<T>(H0[rr * HW]), scx, zb, z);
+                hy = fused_hy(cvt<T>(H0[HCS + rr * HW]), scy, zb, z, Boy, nby);
+                hz = fused_hz(cvt<T>(H0[2 * HCS + rr * HW]), scz, zb, z, Boz, nbz);
+            };
+
+            float4 ce[TY];   // coefficient rows of the lane's nodes, fetched first
+#pragma unroll
+            for (int r = 0; r < TY; ++r) {
+                ce[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (full_plane && own_col && j0 + r < iy1) {
+                    const int id = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + ccol]
+                                        : (int)C0[r * St::C8W + ccol];
+                    ce[r] = __ldg(ctab + id);
                 }
             }
-            if (col_duty) {   // node (i0-1, j0+lx): smem column sx = 0, row lx+1
-                const int cy = lx + 1;
-                if (col_calc) {
-                    const float scy = curl2(sE[s1][0][cy][0], sE[s0][0][cy][0], sE[s0][2][cy][1], sE[s0][2][cy][0], Sz, Sx);
-                    const float scz = curl2(sE[s0][1][cy][1], sE[s0][1][cy][0], sE[s0][0][cy + 1][0], sE[s0][0][cy][0], Sx, Sy);
-                    float d;
-                    sH[1][cy][0] = fused_hy(cur.chy, scy, zb, z, cur.cby, d);
-                    sH[2][cy][0] = fused_hz(cur.chz, scz, zb, z, cur.cbz, d);
+            float px = 0.f, py = 0.f, pz = 0.f;   // H~ at (c, j-1)
+            if (full_plane) {
+                float d0, d1;
+                if (row_slab || col_slab) {
+                    const T *g = gp;
+                    px = Io<T>::ld(g + 3 * NN); py = Io<T>::ld(g + 4 * NN); pz = Io<T>::ld(g + 5 * NN);
                 } else {
-                    sH[1][cy][0] = cur.chy;
-                    sH[2][cy][0] = cur.chz;
+                    hnode(0, true, px, py, pz, d0, d1);
                 }
             }
-            __syncthreads();
-            if (own) {
-                const long long q = (long long)k * P + (long long)j * X + i;
-                const float4 ce = __ldg(B->ctab + cur.cid);
-                const float scx = curl2(sH[2][sy][sx], sH[2][sy - 1][sx], hyv, hym, Sy, Sz);
-                const float scy = curl2(hxv, hxm, sH[2][sy][sx], sH[2][sy][sx - 1], Sz, Sx);
-                const float scz = curl2(sH[1][sy][sx], sH[1][sy][sx - 1], sH[0][sy][sx], sH[0][sy - 1][sx], Sx, Sy);
-                float exv, eyv, ezv;
-                if (!zb) {
-                    exv = __fmaf_rn(ce.x, scx, sE[s0][0][sy][sx]);
-                    eyv = __fmaf_rn(ce.y, scy, sE[s0][1][sy][sx]);
-                    ezv = __fmaf_rn(ce.z, scz, sE[s0][2][sy][sx]);
+#pragma unroll
+            for (int r = 0; r < TY; ++r) {
+                const int j = j0 + r;
+                float hx, hy, hz, nby = 0.f, nbz = 0.f;
+                if (col_slab) {
+                    const T *g = gp + (long long)(r + 1) * X;
+                    hx = Io<T>::ld(g + 3 * NN); hy = Io<T>::ld(g + 4 * NN); hz = Io<T>::ld(g + 5 * NN);
                 } else {
-                    float nd, ndy, ndz;
-                    exv = upml_e2(sE[s0][0][sy][sx], scx, ce.x, kOne, z.zi, kOne, false, 0.f, nd);
-                    eyv = upml_e2(sE[s0][1][sy][sx], scy, ce.y, z.zi, kOne, kOne, true, cur.dy, ndy);
-                    ezv = upml_e2(sE[s0][2][sy][sx], scz, ce.z, kOne, kOne, z.zh, true, cur.dz, ndz);
-                    const long long a = zaux_index(B, zb, i, j, k);
-                    B->zD[zb - 1][0][a] = ndy;
-                    B->zD[zb - 1][1][a] = ndz;
-                    B->zB[zb - 1][0][par ^ 1][a] = nby;
-                    B->zB[zb - 1][1][par ^ 1][a] = nbz;
+                    hnode(r + 1, j < iy1, hx, hy, hz, nby, nbz);
                 }
-                Io<T>::st(F.ohx + q, hxv);
-                Io<T>::st(F.ohy + q, hyv);
-                Io<T>::st(F.ohz + q, hzv);
-                Io<T>::st(F.oex + q, exv);
-                Io<T>::st(F.oey + q, eyv);
-                Io<T>::st(F.oez + q, ezv);
+                const float hyl = __shfl_up_sync(0xffffffffu, hy, 1);   // H~ at (c-1, j)
+                const float hzl = __shfl_up_sync(0xffffffffu, hz, 1);
+                if (full_plane && own_col && j < iy1) {
+                    const int rr = r + 1;
+                    const float4 cr = ce[r];
+                    const float scx = curl2(hz, pz, hy, hk1y[r], Sy, Sz);
+                    const float scy = curl2(hx, hk1x[r], hz, hzl, Sz, Sx);
+                    const float scz = curl2(hy, hyl, hx, px, Sx, Sy);
+                    const float exo = cvt<T>(E0[rr * EW]), eyo = cvt<T>(E0[ECS + rr * EW]), ezo = cvt<T>(E0[2 * ECS + rr * EW]);
+                    float exv, eyv, ezv;
+                    T *o = gp + (long long)rr * X;
+                    if (!zb) {
+                        exv = __fmaf_rn(cr.x, scx, exo);
+                        eyv = __fmaf_rn(cr.y, scy, eyo);
+                        ezv = __fmaf_rn(cr.z, scz, ezo);
+                    } else {
+                        const long long a = za + (long long)rr * zrow;
+                        float nd, ndy, ndz;
+                        exv = upml_e2(exo, scx, cr.x, kOne, z.zi, kOne, false, 0.f, nd);
+                        eyv = upml_e2(eyo, scy, cr.y, z.zi, kOne, kOne, true, ax.dy[r], ndy);
+                        ezv = upml_e2(ezo, scz, cr.z, kOne, kOne, z.zh, true, ax.dz[r], ndz);
+                        zdy[a] = ndy;
+                        zdz[a] = ndz;
+                        nzby[a] = nby;
+                        nzbz[a] = nbz;
+                    }
+                    Io<T>::st(o + 3 * NN, hx);
+                    Io<T>::st(o + 4 * NN, hy);
+                    Io<T>::st(o + 5 * NN, hz);
+                    Io<T>::st(o, exv);
+                    Io<T>::st(o + NN, eyv);
+                    Io<T>::st(o + 2 * NN, ezv);
+                }
+                hk1x[r] = hx;
+                hk1y[r] = hy;
+                px = hx; py = hy; pz = hz;
             }
-            hxm = hxv;
-            hym = hyv;
-            if (more) {
-                store_plane(s2, rE);
-                cur = nxt;
-            }
-            __syncthreads();
+            (void)py;
+            ax = axn;
+            __syncwarp();
+            if (lx == 0) mbar_arrive(&empty[s0]);
+            s0 = s1;
+            s1 = s1 + 1 == NS ? 0 : s1 + 1;
         }
+        __syncwarp();
+        if (lx == 0) mbar_arrive(&empty[s0]);   // the E-only plane above the segment
+        sq = s1;
     }
 }
 
@@ -729,6 +889,54 @@ __global__ void k_energy_final(const double *partials, int n, double *out2)
 }
 
 // ------------------------------------------------------------------ launchers
+// Fused-kernel configurations: W compute warps x 31 columns by TY rows.
+template <int TY, int W>
+struct FusedTune {
+    static constexpr int NS = 4;
+};
+
+template <typename T, int TY, int W>
+struct FusedCfg {
+    static constexpr int NS = FusedTune<TY, W>::NS;
+    using L = FusedLayout<T, TY, W, NS>;
+    static dim3 block() { return dim3(32, W + 1); }
+    static int grid()
+    {
+        static int g = 0;
+        if (!g) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS>, 32 * (W + 1), L::BYTES);
+            g = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+        }
+        return g;
+    }
+    static cudaError_t set_limit()
+    {
+        return cudaFuncSetAttribute(k_fused<T, TY, W, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    }
+    static void launch(const Plan &plan, cudaStream_t st)
+    {
+        const int g = (int)(plan.n_int < grid() ? plan.n_int : grid());
+        cudaMemsetAsync(plan.work, 0, sizeof(int), st);
+        k_fused<T, TY, W, NS><<<g, block(), L::BYTES, st>>>(plan);
+    }
+};
+
+// Supported fused tiles (tile_x columns x tile_y rows): 62x4, 62x8, 124x4, 124x8.
+template <typename T>
+static void launch_fused(const Plan &plan, cudaStream_t st)
+{
+    const int key = plan.tile_x * 16 + plan.tile_y;
+    switch (key) {
+    case 62 * 16 + 4: FusedCfg<T, 4, 2>::launch(plan, st); break;
+    case 62 * 16 + 8: FusedCfg<T, 8, 2>::launch(plan, st); break;
+    case 124 * 16 + 8: FusedCfg<T, 8, 4>::launch(plan, st); break;
+    default: FusedCfg<T, 4, 4>::launch(plan, st); break;
+    }
+}
+
 template <typename T>
 static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream_t st)
 {
@@ -738,12 +946,7 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
             k_slab_h<T><<<(int)(plan.n_slab < grid_cap ? plan.n_slab : grid_cap), kSlabThreads, 0, st>>>(plan);
         break;
     case kPhaseInterior:
-        if (plan.n_int > 0) {
-            const int g = (int)(plan.n_int < grid_cap ? plan.n_int : grid_cap);
-            if (plan.tile_y == 2) k_fused<T, 2><<<g, dim3(32, 2), 0, st>>>(plan);
-            else if (plan.tile_y == 8) k_fused<T, 8><<<g, dim3(32, 8), 0, st>>>(plan);
-            else k_fused<T, 4><<<g, dim3(32, 4), 0, st>>>(plan);
-        }
+        if (plan.n_int > 0) launch_fused<T>(plan, st);
         break;
     case kPhaseSlabE:
         if (plan.n_slab > 0)
@@ -772,6 +975,24 @@ cudaError_t launch_step(const Plan &plan, int prec, int grid_cap, cudaStream_t s
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (ty == 4 || ty == 8); }
+
+template <typename T>
+static cudaError_t limits_t()
+{
+    cudaError_t e[4] = {FusedCfg<T, 4, 2>::set_limit(), FusedCfg<T, 8, 2>::set_limit(), FusedCfg<T, 4, 4>::set_limit(),
+                        FusedCfg<T, 8, 4>::set_limit()};
+    for (cudaError_t x : e)
+        if (x != cudaSuccess) return x;
+    return cudaSuccess;
+}
+
+cudaError_t fused_set_smem_limits()
+{
+    cudaError_t a = limits_t<float>(), b = limits_t<__half>(), c = limits_t<__nv_bfloat16>();
+    return a != cudaSuccess ? a : (b != cudaSuccess ? b : c);
 }
 
 cudaError_t launch_dft(const Plan &plan, int grid_cap, cudaStream_t st)

@@ -6,7 +6,7 @@ Tolerances (FP32 arithmetic against FP64):
     every element within 1e-4 of that component's max |value|;
   * FP16 / BF16 storage (FP32 arithmetic): probe-trace relative L2 <= 1e-2;
   * resonant peaks of the spectra: the same FFT bin.
-Sizes span several fused tiles (32 x 4 columns, z-segments of 16) with
+Sizes span several fused tiles (124 x 4 columns, z-segments of 50) with
 ragged tails in every axis, the UPML on all faces, PEC sheets, PMC walls.
 """
 import numpy as np
@@ -159,8 +159,9 @@ def test_chunking_and_tiling_do_not_change_results(fdtd):
     z-segments (halo recomputation equals the owner's value)."""
     p = W.random_problem(6, 45, 38, 29, upml=4, n_steps=50)
     outs = []
-    for tune in [dict(tile_x=32, tile_y=4, zseg=16, graph_chunk=16), dict(tile_x=32, tile_y=2, zseg=5, graph_chunk=1),
-                 dict(tile_x=32, tile_y=8, zseg=64, graph_chunk=7), dict(tile_x=32, tile_y=4, zseg=3, graph_chunk=4)]:
+    for tune in [dict(tile_x=124, tile_y=4, zseg=16, graph_chunk=16), dict(tile_x=62, tile_y=4, zseg=5, graph_chunk=1),
+                 dict(tile_x=62, tile_y=8, zseg=64, graph_chunk=7), dict(tile_x=124, tile_y=8, zseg=3, graph_chunk=4),
+                 dict(tile_x=124, tile_y=4, zseg=9, graph_chunk=16)]:
         s = fdtd.Solver(p, tuning=tune)
         s.run()
         outs.append([s.field(c) for c in range(6)])
