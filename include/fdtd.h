@@ -200,6 +200,32 @@ const char *fdtd_strerror(int code);
 /* Text of the last FDTD_EINVAL / FDTD_ECUDA raised on this host thread. */
 const char *fdtd_last_error(void);
 
+/* Discrete field energy and max |div B| of fields the caller owns, with no
+ * device allocation.  The paper has no counterpart: this is a service for
+ * callers that cannot allocate device memory when they need the check --
+ * code running while a stream is captured into a CUDA graph, code under a
+ * fixed memory budget or pool, real-time loops that forbid allocator calls.
+ * It computes the same quantities as fdtd_diagnostics, from raw arrays:
+ *  fields   9 device pointers to FP32 [nz+1][ny+1][pitch] arrays (x fastest,
+ *           node layout as fdtd_get_field): E^n x,y,z [V/m], H^{n-1/2} x,y,z
+ *           and H^{n+1/2} x,y,z [A/m]
+ *  eps_r    3 device pointers to the per-edge relative permittivity of the
+ *           E_x, E_y, E_z edges in the same layout, or NULL (all 1)
+ *  nx,ny,nz cells; pitch >= nx+1 elements; dx,dy,dz cell sizes [m]
+ *  upml_depth  6 UPML depths (NULL: none): div B is taken over cells outside
+ *  stream   cudaStream_t to run on (NULL: legacy default stream)
+ *  energy, max_div_b  host outputs [J] and [T/m] (either may be NULL)
+ * Scratch space is a fixed static device array that each GPU loading the
+ * library holds until exit; grids above 33,554,432 nodes are rejected with
+ * FDTD_EINVAL.  The first call on a device resolves the array's device
+ * address with that device current, so it must come before any stream
+ * capture.  All calls share the array: calls whose work overlaps on the GPU
+ * race.  Synchronises the stream; errors as the other calls (message from
+ * fdtd_last_error). */
+int fdtd_energy_static(const float *const fields[9], const float *const eps_r[3], int nx, int ny, int nz,
+                       int pitch, double dx, double dy, double dz, const int upml_depth[6], void *stream,
+                       double *energy, double *max_div_b);
+
 /* ---------------- batching (many boards, one launch per phase) -------------
  * A batch steps many boards with one kernel launch per phase (UPML H, interior
  * fused H+E, UPML E, sources/probes) over a packed list of (board, tile) work

@@ -74,6 +74,8 @@ _SIGS = {
     "fdtd_destroy": (None, [c_void_p]),
     "fdtd_strerror": (ctypes.c_char_p, [c_int]),
     "fdtd_last_error": (ctypes.c_char_p, []),
+    "fdtd_energy_static": (c_int, [P(c_void_p), P(c_void_p), c_int, c_int, c_int, c_int, c_double, c_double,
+                                   c_double, P(c_int), c_void_p, P(c_double), P(c_double)]),
     "fdtd_batch_create": (c_int, [c_void_p, P(c_void_p)]),
     "fdtd_batch_add": (c_int, [c_void_p, c_void_p, c_int]),
     "fdtd_batch_remove": (c_int, [c_void_p, c_void_p]),

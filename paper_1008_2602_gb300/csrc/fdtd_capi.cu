@@ -60,6 +60,12 @@ int elem_size(int prec) { return prec == FDTD_FP32 ? 4 : 2; }
 
 }  // namespace
 
+int fdtd::set_error(int code, const char *msg)
+{
+    g_err = msg ? msg : "";
+    return code;
+}
+
 struct fdtd_batch;
 
 struct fdtd_ctx {

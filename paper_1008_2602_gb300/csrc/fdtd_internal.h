@@ -157,6 +157,8 @@ cudaError_t launch_energy(const Board *b_dev, const Board &b_host, double *parti
                           double *out2, cudaStream_t st);
 int energy_partials(const Board &b_host);
 bool fused_tile_supported(int tile_x, int tile_y);
+// Record the message returned by fdtd_last_error on this thread; returns code.
+int set_error(int code, const char *msg);
 cudaError_t fused_set_smem_limits();
 
 }  // namespace fdtd
