@@ -277,6 +277,146 @@ def cpu_baseline(args, sample_steps: int):
                       f"(FP64, OpenMP {n} threads, setup included)"}
 
 
+def _plain_solves(probs, precision, tuning=None):
+    """Each board solved alone, one after the other (per-board launches)."""
+    from paper_1008_2602_gb300 import solver
+    t0 = time.perf_counter()
+    out = []
+    for p in probs:
+        s = solver.Solver(p, precision=precision, tuning=tuning)
+        s.run()
+        out.append(s.traces())
+        s.close()
+    return time.perf_counter() - t0, out
+
+
+def run_batched(args, world, rank, local):
+    """64 uneven boards (plane sides 20-120 mm, 1-3 pairs, dx=0.5 mm,
+    5000 steps each) in one batch; a bench step is one full batched solve."""
+    import numpy as np
+    import torch
+    from paper_1008_2602_gb300 import solver, tune, workloads as W
+    torch.cuda.set_device(local)
+    probs = W.batch_boards(seed=4 + 100 * rank, n_boards=args.boards, n_steps=args.batch_steps)
+    # tuned on the first 8 boards of the batch (same board distribution), cached per grid class
+    tuning = tune.tune(probs[:8], args.precision, steps=16, log=lambda m: print(m, file=sys.stderr))
+    cells = sum(p.cells * p.n_steps for p in probs)
+
+    def batched_solve():
+        b = solver.Batch(tuning=tuning)
+        sols = [solver.Solver(p, precision=args.precision) for p in probs]
+        for s_ in sols:
+            b.add(s_)
+        done = 0
+        while done < len(sols):
+            done = b.step(args.window)
+        b.sync()
+        return b, sols
+
+    for _ in range(args.warmup):
+        b, sols = batched_solve()
+        b.close()
+        for s_ in sols:
+            s_.close()
+    if world > 1:
+        torch.distributed.barrier()
+    times, last = [], None
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b, sols = batched_solve()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+            if last is not None:
+                for s_ in last[1]:
+                    s_.close()
+                last[0].close()
+            last = (b, sols)
+    el = sum(times)
+    if world > 1:
+        t = torch.tensor([el], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        el = float(t.item())
+    value = len(probs) * args.steps * world / el
+    # per-board plain launches on the same GPU, and identity of the results
+    plain_t, plain_tr = _plain_solves(probs[: args.plain_boards], args.precision)
+    plain_rate = args.plain_boards / plain_t
+    diffs = [float(np.abs(last[1][q].traces() - plain_tr[q]).max()) for q in range(args.plain_boards)]
+    for s_ in last[1]:
+        s_.close()
+    last[0].close()
+    return {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
+            f"{args.precision}-storage/f32-compute", "data": "synthetic (seeded boards, sources, probes)",
+            "config": {"workload": f"batched: {len(probs)} boards (plane sides 20-120 mm, 1-3 pairs, dx=dy=0.5 mm, "
+                                   f"dz=0.2 mm, 6-cell air, 10-cell UPML), {args.batch_steps} steps each; "
+                                   "step = one batched solve of all boards",
+                       "cells_total": int(sum(p.cells for p in probs)), "tuning": tuning,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "gcell_updates_per_s": round(cells * args.steps * world / el / 1e9, 3),
+            "per_board_plain": {"solves_per_s": round(plain_rate, 4), "boards_timed": args.plain_boards,
+                                "speedup_batched": round(value / world / plain_rate, 3)},
+            "batched_vs_alone_max_abs_trace_diff": max(diffs),
+            "gpu_launches": None, "clocks": clk.summary(), "e2e": None}
+
+
+def run_served(args, world, rank, local):
+    """Poisson request stream (mean 20 req/s) of multilayer boards, admitted by
+    HBM budget into one continuously batched mix; p50/p99 latency."""
+    import torch
+    from paper_1008_2602_gb300 import serve, workloads as W
+    torch.cuda.set_device(local)
+    reqs = W.request_stream(seed=5 + 100 * rank, n_requests=args.requests, rate=args.rate,
+                            step_scale=args.step_scale, cell_scale=args.cell_scale)
+    warm = W.request_stream(seed=99, n_requests=4, rate=1000.0, step_scale=0.02, cell_scale=0.05)
+    be = serve.CudaBackend(precision=args.precision)
+    serve.Server(be, hbm_budget=int(args.hbm_budget_gb * 2**30), chunk=args.window).run(warm)
+    be.close()
+    if world > 1:
+        torch.distributed.barrier()
+    be = serve.CudaBackend(precision=args.precision)
+    srv = serve.Server(be, hbm_budget=int(args.hbm_budget_gb * 2**30), chunk=args.window)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        res = srv.run(reqs)
+        wall = time.perf_counter() - t0
+    be.close()
+    summ = serve.summarize(res, wall)
+    # the same stream served one request at a time (per-board plain launches)
+    from paper_1008_2602_gb300 import solver
+    t0 = time.perf_counter()
+    lat = []
+    start = time.perf_counter()
+    for r in reqs[: args.plain_requests]:
+        now = time.perf_counter() - start
+        if now < r.arrival:
+            time.sleep(r.arrival - now)
+        s_ = solver.Solver(r.problem, precision=args.precision)
+        s_.run()
+        s_.spectra()
+        s_.close()
+        lat.append(time.perf_counter() - start - r.arrival)
+    plain_wall = time.perf_counter() - t0
+    import numpy as np
+    return {"metric": METRIC, "value": round(summ["solves_per_s"], 4), "unit": "solves/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": round(wall * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.precision == "fp32" else f"{args.precision}-storage/f32-compute",
+            "data": "synthetic (seeded Poisson stream of boards)",
+            "config": {"workload": f"served: {args.requests} requests, Poisson {args.rate} req/s, lognormal cells "
+                                   f"(median {2e6 * args.cell_scale:.3g}, max {40e6 * args.cell_scale:.3g}), "
+                                   f"{int(2000 * args.step_scale)}-{int(20000 * args.step_scale)} steps, 4-32 probes",
+                       "chunk_steps": args.window, "hbm_budget_gb": args.hbm_budget_gb,
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "served": summ,
+            "per_request_plain": {"requests": len(lat), "solves_per_s": round(len(lat) / plain_wall, 4),
+                                  "p50_latency_s": float(np.percentile(lat, 50)),
+                                  "p99_latency_s": float(np.percentile(lat, 99))},
+            "gpu_launches": None, "clocks": clk.summary(), "e2e": None}
+
+
 def run_reference(args, world, rank):
     """Reference arm: the FP64 oracle timed as it stands on the host cores."""
     if rank != 0:
@@ -312,7 +452,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="multilayer", choices=["small", "realistic", "multilayer", "multilayer_h", "multilayer_q"])
+    ap.add_argument("--workload", default="multilayer",
+                    choices=["small", "realistic", "multilayer", "multilayer_h", "multilayer_q", "batched", "served"])
+    ap.add_argument("--boards", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=5000)
+    ap.add_argument("--plain-boards", type=int, default=16)
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--step-scale", type=float, default=1.0)
+    ap.add_argument("--cell-scale", type=float, default=1.0)
+    ap.add_argument("--plain-requests", type=int, default=16)
+    ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--window", type=int, default=200)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
     ap.add_argument("--tile-x", type=int, default=0, help="fused tile width (32, 64, 128); 0 = tuned default")
@@ -334,6 +484,15 @@ def main():
         out = run_reference(args, world, rank)
         if out is not None:
             print(json.dumps(out), flush=True)
+        return
+    if args.workload in ("batched", "served"):
+        out = (run_batched if args.workload == "batched" else run_served)(args, world, rank, local)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        if world > 1:
+            import torch
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
         return
     out = run_single(args, world, rank, local)
     if rank == 0:

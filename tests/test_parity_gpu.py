@@ -250,3 +250,44 @@ def test_unstable_courant_is_detected(fdtd):
         s.sync()
     assert ei.value.code == capi.FDTD_EUNSTABLE
     s.close()
+
+
+def test_served_results_equal_alone(fdtd):
+    """Requests arriving at staggered times join a running mix (continuous
+    batching); every request's spectrum equals the same board solved alone."""
+    from paper_1008_2602_gb300 import serve
+    reqs = W.request_stream(seed=21, n_requests=6, rate=400.0, step_scale=0.03, cell_scale=0.01)
+    alone = {}
+    for r in reqs:
+        s = fdtd.Solver(r.problem)
+        s.run()
+        alone[r.rid] = s.spectra()
+        s.close()
+    be = serve.CudaBackend()
+    srv = serve.Server(be, hbm_budget=8 << 30, chunk=37)
+    res = srv.run(reqs)
+    be.close()
+    assert sorted(x.rid for x in res) == sorted(alone)
+    for x in res:
+        ref = alone[x.rid]
+        assert x.spectra.shape == ref.shape
+        assert np.abs(x.spectra - ref).max() <= 1e-12 * np.abs(ref).max(), x.rid
+    assert max(x.latency for x in res) > 0
+
+
+def test_autotuner_picks_a_valid_configuration(fdtd, tmp_path, monkeypatch):
+    """The tuner times candidate launch shapes on throwaway copies and returns
+    one the library accepts; the tuned run gives the same fields."""
+    from paper_1008_2602_gb300 import tune
+    monkeypatch.setattr(tune, "CACHE", str(tmp_path / "tune.json"))
+    rng = np.random.default_rng(3)
+    probs = [W.batch_board(rng, n_steps=60, dxy=2e-3, dz=0.4e-3, upml=(6, 6, 6), size_mm=(30, 60)) for _ in range(3)]
+    cfg = tune.tune(probs, steps=6, zsegs=[16, 50], chunks=[16])
+    assert (cfg["tile_x"], cfg["tile_y"]) in tune.SHAPES
+    a = fdtd.Solver(probs[0], tuning=cfg)
+    a.run()
+    b = fdtd.Solver(probs[0])
+    b.run()
+    assert np.array_equal(a.field(2), b.field(2))
+    assert tune.tune(probs, steps=6) == cfg   # cached
+    a.close(); b.close()

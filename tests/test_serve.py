@@ -1,0 +1,94 @@
+"""Host-side logic of the continuous-batching server, with a fake backend
+and a simulated clock (no GPU): admission by HBM budget and slot count,
+arrival order, chunked progress, latency accounting, rejection of requests
+that can never fit."""
+import numpy as np
+
+from paper_1008_2602_gb300 import serve, workloads as W
+
+
+class FakeBackend:
+    precision = "fp32"
+
+    def __init__(self, cells_per_s=1e10):
+        self.rate = cells_per_s
+        self.active = []
+        self.max_active = 0
+        self.order = []
+
+    def admit(self, prob):
+        h = {"prob": prob, "left": prob.n_steps}
+        self.active.append(h)
+        self.order.append(prob.name)
+        self.max_active = max(self.max_active, len(self.active))
+        self.max_bytes = max(getattr(self, "max_bytes", 0), sum(self.device_bytes(a) for a in self.active))
+        return h
+
+    def device_bytes(self, h):
+        return serve.estimate_bytes(h["prob"])
+
+    def step(self, n):
+        work = 0.0
+        for h in self.active:
+            d = min(n, h["left"])
+            h["left"] -= d
+            work += d * h["prob"].cells
+        return work / self.rate
+
+    def remaining(self, h):
+        return h["left"]
+
+    def retire(self, h):
+        self.active.remove(h)
+        return np.zeros(1)
+
+
+def _reqs(n=12, rate=20.0, seed=5):
+    return W.request_stream(seed=seed, n_requests=n, rate=rate, step_scale=0.05, cell_scale=0.02)
+
+
+def test_all_requests_served_in_arrival_order():
+    reqs = _reqs()
+    be = FakeBackend()
+    srv = serve.Server(be, hbm_budget=1 << 40, chunk=50, simulate_clock=True)
+    res = srv.run(reqs)
+    assert sorted(r.rid for r in res) == [r.rid for r in reqs]
+    assert be.order == [r.problem.name for r in reqs]
+    for r in res:
+        assert r.finished >= r.admitted >= r.arrival - 1e-12
+        assert r.latency > 0
+
+
+def test_budget_limits_concurrency():
+    reqs = _reqs(n=10, rate=1e6)   # all arrive at once
+    need = max(serve.estimate_bytes(r.problem) for r in reqs)
+    be = FakeBackend()
+    srv = serve.Server(be, hbm_budget=int(2.5 * need), chunk=50, simulate_clock=True)
+    res = srv.run(reqs)
+    assert len(res) == 10
+    assert be.max_bytes <= int(2.5 * need)      # admitted bytes never exceed the budget
+    assert 2 <= be.max_active < 10
+
+
+def test_slot_limit_and_continuous_admission():
+    reqs = _reqs(n=9, rate=1e6)
+    be = FakeBackend()
+    srv = serve.Server(be, hbm_budget=1 << 40, max_boards=3, chunk=25, simulate_clock=True)
+    srv.run(reqs)
+    assert be.max_active == 3
+
+
+def test_oversized_request_is_rejected_not_hung():
+    reqs = _reqs(n=4)
+    be = FakeBackend()
+    tiny = min(serve.estimate_bytes(r.problem) for r in reqs) - 1
+    srv = serve.Server(be, hbm_budget=tiny, chunk=50, simulate_clock=True)
+    res = srv.run(reqs)
+    assert res == [] and sorted(srv.rejected) == [r.rid for r in reqs]
+
+
+def test_summary_percentiles():
+    rs = [serve.Result(rid=i, arrival=0.0, admitted=0.0, finished=float(i + 1), cells=10, steps=10) for i in range(100)]
+    s = serve.summarize(rs, wall=100.0)
+    assert abs(s["p50_latency_s"] - 50.5) < 1e-9 and s["p99_latency_s"] > 99.0
+    assert abs(s["solves_per_s"] - 1.0) < 1e-12
