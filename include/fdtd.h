@@ -147,10 +147,12 @@ int fdtd_set_spectrum(fdtd_ctx *ctx, double f_max, int n_total_steps);
 int fdtd_step(fdtd_ctx *ctx, int n);
 
 /* fdtd_step with every phase launched directly (no CUDA graph) and timed
- * with CUDA events on the context's stream: phase_ms[0..4] receive the summed
- * device time [ms] of the UPML/boundary slab H kernel, the interior fused
- * H+E kernel, the slab E kernel, the source/probe kernel and the running-DFT
- * update over the n steps.  Synchronises.  phase_ms may not be NULL. */
+ * with CUDA events on the context's stream: phase_ms[0..5] receive the summed
+ * device time [ms] of the UPML/boundary slab H kernel, the fused H+E kernel
+ * over the z-UPML planes of the interior columns, the fused H+E kernel over
+ * the interior planes, the slab E kernel, the source/probe kernel and the
+ * running-DFT update over the n steps.  Synchronises.  phase_ms (6 doubles)
+ * may not be NULL. */
 int fdtd_step_profiled(fdtd_ctx *ctx, int n, double *phase_ms);
 
 /* Copy the running DFT to host out[P][Q][2] (re, im), P = probes, Q = bins;

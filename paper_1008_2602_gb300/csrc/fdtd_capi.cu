@@ -460,7 +460,7 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
         if (!c->zplanes[bx]) continue;
         for (int a = 0; a < 2; ++a) {
             if (int r = encode3d(&maps[tm_zd(bx, a)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zD[bx][a], h.zpitch, Ly,
-                                 c->zplanes[bx], box_a(tx), ty + 1))
+                                 c->zplanes[bx], box_a(tx), ty))
                 return r;
             for (int par = 0; par < 2; ++par)
                 if (int r = encode3d(&maps[tm_zb(bx, a, par)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zB[bx][a][par],
@@ -479,11 +479,16 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
     return upload_board(c);
 }
 
-long long interior_items(const Board &h, const fdtd_tuning &t)
+// Fused-kernel items of a board: (x tile, y tile, z segment), x fastest.  The
+// interior launch covers planes [iz0, iz1), the z-UPML launch [1, iz0) and
+// [max(iz1, iz0), nz); the device decodes items the same way.
+long long fused_items(const Board &h, const fdtd_tuning &t, bool zp)
 {
-    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
-    if (Lx <= 0 || Ly <= 0 || Lz <= 0) return 0;
-    return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * ((Lz + t.zseg - 1) / t.zseg);
+    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0;
+    if (Lx <= 0 || Ly <= 0 || h.nz < 2) return 0;
+    auto segs = [&](long long k0, long long k1) { return k1 > k0 ? (k1 - k0 + t.zseg - 1) / t.zseg : 0; };
+    const long long nseg = zp ? segs(1, h.iz0) + segs(std::max(h.iz1, h.iz0), h.nz) : segs(h.iz0, h.iz1);
+    return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * nseg;
 }
 
 long long dft_items(const Board &h)
@@ -492,18 +497,19 @@ long long dft_items(const Board &h)
     return (long long)h.n_bins * ((h.n_probe + kDftProbeGroup - 1) / kDftProbeGroup);
 }
 
-// Lay out plan arrays [boards | int_prefix | slab_prefix | dft_prefix] in buf.
+// Lay out plan arrays [boards | int_prefix | zp_prefix | slab_prefix | dft_prefix | work] in buf.
 int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long long *&buf, size_t &cap,
                Plan &plan, cudaStream_t st, std::vector<long long> &host)
 {
     const int nb = (int)boards.size();
-    const size_t words = (size_t)nb + 3 * ((size_t)nb + 1) + 1;   // + work counter
+    const size_t words = (size_t)nb + 4 * ((size_t)nb + 1) + 1;   // + two work counters
     host.assign(words, 0);
     long long *ptrs = host.data();
-    long long *ip = ptrs + nb, *sp = ip + nb + 1, *dp = sp + nb + 1;
+    long long *ip = ptrs + nb, *zp = ip + nb + 1, *sp = zp + nb + 1, *dp = sp + nb + 1;
     for (int b = 0; b < nb; ++b) {
         ptrs[b] = (long long)(uintptr_t)boards[b]->d;
-        ip[b + 1] = ip[b] + interior_items(boards[b]->h, t);
+        ip[b + 1] = ip[b] + fused_items(boards[b]->h, t, false);
+        zp[b + 1] = zp[b] + fused_items(boards[b]->h, t, true);
         sp[b + 1] = sp[b] + boards[b]->h.slab_blocks;
         dp[b + 1] = dp[b] + dft_items(boards[b]->h);
     }
@@ -525,12 +531,14 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.zseg = t.zseg;
     plan.boards = (Board *const *)buf;
     plan.int_prefix = buf + nb;
-    plan.slab_prefix = buf + nb + (nb + 1);
-    plan.dft_prefix = buf + nb + 2 * (nb + 1);
+    plan.zp_prefix = buf + nb + (nb + 1);
+    plan.slab_prefix = buf + nb + 2 * (nb + 1);
+    plan.dft_prefix = buf + nb + 3 * (nb + 1);
     plan.n_int = ip[nb];
+    plan.n_zp = zp[nb];
     plan.n_slab = sp[nb];
     plan.n_dft = dp[nb];
-    plan.work = (int *)(buf + nb + 3 * (nb + 1));
+    plan.work = (int *)(buf + nb + 4 * (nb + 1));
     return FDTD_OK;
 }
 
@@ -1124,7 +1132,7 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     info->precision = c->prec;
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
     info->interior_nodes = (Lx > 0 && Ly > 0 && Lz > 0) ? Lx * Ly * Lz : 0;
-    info->fused_upml_nodes = (long long)(c->zaux_n[0] + c->zaux_n[1]);
+    info->fused_upml_nodes = info->interior_nodes > 0 ? Lx * Ly * (c->zplanes[0] + c->zplanes[1]) : 0;
     long long sn = 0;
     for (int s = 0; s < h.n_slab; ++s) sn += h.slab[s].n;
     info->slab_nodes = sn;

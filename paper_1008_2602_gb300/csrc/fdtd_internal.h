@@ -121,19 +121,20 @@ struct Plan {
     int nb;
     int tile_x, tile_y, zseg;     // interior tile (threads in x, y) and z-segment
     Board *const *boards;         // [nb] device pointers
-    const long long *int_prefix;  // [nb + 1] interior tiles
+    const long long *int_prefix;  // [nb + 1] interior-kernel items (planes [iz0, iz1))
+    const long long *zp_prefix;   // [nb + 1] z-UPML-kernel items (planes [1, iz0) and [iz1, nz))
     const long long *slab_prefix; // [nb + 1] slab blocks
     const long long *dft_prefix;  // [nb + 1] DFT warps
-    long long n_int, n_slab, n_dft;
-    int *work;                    // fused-kernel work counter (zeroed before every launch)
+    long long n_int, n_zp, n_slab, n_dft;
+    int *work;                    // fused-kernel work counters [interior, z-UPML] (zeroed before every launch)
 };
 
 // TMA descriptor slots of a board (3D maps: x, y, plane).
-__host__ __device__ constexpr int tm_e(int par, int c) { return par * 3 + c; }               // E box  48 x (TY+2)
-__host__ __device__ constexpr int tm_h(int par, int c) { return 6 + par * 3 + c; }           // H box  40 x (TY+1)
-constexpr int kTmCid = 12;                                                // ids    48|40 x TY
-__host__ __device__ constexpr int tm_zd(int box, int a) { return 13 + box * 2 + a; }         // D~     40 x (TY+1)
-__host__ __device__ constexpr int tm_zb(int box, int a, int par) { return 17 + (box * 2 + a) * 2 + par; }   // B~
+__host__ __device__ constexpr int tm_e(int par, int c) { return par * 3 + c; }               // E   box_e  x (TY+2)
+__host__ __device__ constexpr int tm_h(int par, int c) { return 6 + par * 3 + c; }           // H   box_h  x (TY+1)
+constexpr int kTmCid = 12;                                                // ids box_c* x TY
+__host__ __device__ constexpr int tm_zd(int box, int a) { return 13 + box * 2 + a; }         // D~  box_a  x TY
+__host__ __device__ constexpr int tm_zb(int box, int a, int par) { return 17 + (box * 2 + a) * 2 + par; }   // B~ box_a x (TY+1)
 constexpr int kNumMaps = 25;
 // TMA box widths for a tile of tx columns (x rounded down to 16 bytes)
 __host__ __device__ constexpr int box_up(int x, int m) { return (x + m - 1) / m * m; }
@@ -141,12 +142,12 @@ __host__ __device__ constexpr int box_e(int tx) { return box_up(tx + 9, 8); }
 __host__ __device__ constexpr int box_h(int tx) { return box_up(tx + 8, 8); }
 __host__ __device__ constexpr int box_c8(int tx) { return box_up(tx + 15, 16); }
 __host__ __device__ constexpr int box_c16(int tx) { return box_up(tx + 7, 8); }
-__host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 4, 4); }
+__host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 5, 4); }
 
 constexpr int kSlabThreads = 256;
 constexpr int kDftProbeGroup = 4;
 
-enum Phase : int { kPhaseSlabH = 0, kPhaseInterior = 1, kPhaseSlabE = 2, kPhasePost = 3, kNumPhases = 4 };
+enum Phase : int { kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseInterior = 2, kPhaseSlabE = 3, kPhasePost = 4, kNumPhases = 5 };
 
 // Launchers (fdtd_kernels.cu).  All enqueue on `st`.
 cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cudaStream_t st);

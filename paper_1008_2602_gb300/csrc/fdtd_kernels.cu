@@ -203,35 +203,98 @@ __device__ __forceinline__ float cvt<__half>(__half v) { return __half2float(v);
 template <>
 __device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
-// Shared-memory stage of one plane for a tile of W warps x 31 columns by TY
+// Two adjacent elements of one row (8-byte aligned for FP32, 4-byte for the
+// 16-bit storage types), converted to/from FP32.
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    static __device__ __forceinline__ float2 lds(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+    static __device__ __forceinline__ float2 ldg(const float *p) { return __ldg(reinterpret_cast<const float2 *>(p)); }
+    static __device__ __forceinline__ void st(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+};
+template <>
+struct Pair<__half> {
+    static __device__ __forceinline__ float2 lds(const __half *p)
+    {
+        return __half22float2(*reinterpret_cast<const __half2 *>(p));
+    }
+    static __device__ __forceinline__ float2 ldg(const __half *p)
+    {
+        return __half22float2(__ldg(reinterpret_cast<const __half2 *>(p)));
+    }
+    static __device__ __forceinline__ void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
+};
+template <>
+struct Pair<__nv_bfloat16> {
+    static __device__ __forceinline__ float2 lds(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+    }
+    static __device__ __forceinline__ float2 ldg(const __nv_bfloat16 *p)
+    {
+        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
+    }
+    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v)
+    {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
+    }
+};
+
+// Paired forms of curl2 and of h - s.  Per element they round exactly like
+// the scalar forms: a - b == fma(b, -1, a) (the product is exact), and
+// fma(-Sb, d, x) is the same single rounding either way.
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 curl2v(float2 a1, float2 a0, float2 b1, float2 b0, float2 Sa, float2 nSb)
+{
+    return __ffma2_rn(nSb, sub2(b1, b0), __fmul2_rn(Sa, sub2(a1, a0)));
+}
+
+// Columns owned by one compute warp: lane l holds the pair g + 2l, g + 2l + 1
+// with g the even column at or just below the strip's low-x halo.
+constexpr int kWarpCols = 62;
+
+// Shared-memory stage of one plane for a tile of W warps x 62 columns by TY
 // rows.  Boxes start at x rounded down to the 16-byte TMA boundary:
-//   E  3 x (TY+2) x EW   nodes i0-1 .. i0+31W, rows j0-1 .. j0+TY
-//   H  3 x (TY+1) x HW   nodes i0-1 .. i0+31W-1, rows j0-1 .. j0+TY-1
+//   E  3 x (TY+2) x EW   rows j0-1 .. j0+TY
+//   H  3 x (TY+1) x HW   rows j0-1 .. j0+TY-1
 //   id TY x C8W bytes (or TY x C16W uint16), rows j0 .. j0+TY-1
+//   z-UPML kernel only: B~y, B~z (TY+1) x AW and D~y, D~z TY x AW floats
 // Every box starts 128-byte aligned.
-template <typename T, int TY, int W>
+template <typename T, int TY, int W, bool ZP>
 struct Stage {
     static constexpr int al(int x) { return (x + 127) & ~127; }
-    static constexpr int TX = 31 * W;
+    static constexpr int TX = kWarpCols * W;
     static constexpr int ES = (int)sizeof(T);
-    static constexpr int EW = box_e(TX), HW = box_h(TX), C8W = box_c8(TX), C16W = box_c16(TX);
+    static constexpr int EW = box_e(TX), HW = box_h(TX), C8W = box_c8(TX), C16W = box_c16(TX), AW = box_a(TX);
     static constexpr int E_COMP = (TY + 2) * EW, H_COMP = (TY + 1) * HW;
     static constexpr int E_CS = al(E_COMP * ES) / ES, H_CS = al(H_COMP * ES) / ES;
     static constexpr int E_BYTES = 3 * E_COMP * ES;
     static constexpr int H_BYTES = 3 * H_COMP * ES;
     static constexpr int C8_BYTES = TY * C8W, C16_BYTES = TY * C16W * 2;
+    static constexpr int B_COMP = (TY + 1) * AW, D_COMP = TY * AW;
+    static constexpr int B_CS = al(B_COMP * 4) / 4, D_CS = al(D_COMP * 4) / 4;
+    static constexpr int A_BYTES = 2 * (B_COMP + D_COMP) * 4;
     static constexpr int E_OFF = 0;
     static constexpr int H_OFF = 3 * E_CS * ES;
     static constexpr int C_OFF = H_OFF + 3 * H_CS * ES;
-    static constexpr int ITEM_OFF = C_OFF + al(C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES);   // item id of the plane
+    static constexpr int A_OFF = C_OFF + al(C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES);
+    static constexpr int ITEM_OFF = A_OFF + (ZP ? 2 * (B_CS + D_CS) * 4 : 0);   // item id of the plane
     static constexpr int BYTES = ITEM_OFF + 128;
 };
 
-template <typename T, int TY, int W, int NS>
+template <typename T, int TY, int W, int NS, bool ZP>
 struct FusedLayout {
-    using St = Stage<T, TY, W>;
+    using St = Stage<T, TY, W, ZP>;
     static constexpr int BAR_OFF = NS * St::BYTES;
     static constexpr int BYTES = BAR_OFF + 2 * NS * 8 + 16;
+    // blocks per SM that shared memory allows (228 KB per SM, 1 KB reserved
+    // per block); the register budget keeps them resident but never drops
+    // below 128 registers per thread (176 for 8-row tiles)
+    static constexpr int PER_SM = 233472 / (BYTES + 1024);
+    static constexpr int REG_SM = 65536 / ((TY >= 8 ? 176 : 128) * (32 * W + 32));
+    static constexpr int CAP = PER_SM < REG_SM ? PER_SM : REG_SM;
+    static constexpr int MINB = CAP < 1 ? 1 : (CAP > 8 ? 8 : CAP);
 };
 
 __device__ __forceinline__ void mbar_arrive(uint64_t *b)
@@ -246,47 +309,73 @@ struct Tile {
     int i0, j0, kb, ke, kstart, par;
 };
 
-template <int TY, int W>
+// Items of one board: x tiles fastest, then y tiles, then z segments.  The
+// interior kernel (ZP false) covers planes [iz0, iz1); the z-UPML kernel
+// covers [1, iz0) and [max(iz1, iz0), nz).  kstart is the plane below the
+// segment when the tile recomputes its H~ there, else kb (that plane's H~ is
+// then read from the output: an outer plane, or a z-UPML plane written by the
+// z-UPML launch, which runs first).
+template <int TY, int W, bool ZP>
 __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 {
     Tile t;
-    const int b = find_board(plan.int_prefix, plan.nb, item);
+    const long long *prefix = ZP ? plan.zp_prefix : plan.int_prefix;
+    const int b = find_board(prefix, plan.nb, item);
     t.B = plan.boards[b];
     t.ok = board_active(t.B);
     const long long step = *((volatile long long *)t.B->step);
     t.par = (int)(step & 1);
-    const long long local = item - __ldg(plan.int_prefix + b);
-    const int ntx = (t.B->ix1 - t.B->ix0 + 31 * W - 1) / (31 * W), nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
+    const long long local = item - __ldg(prefix + b);
+    constexpr int TX = kWarpCols * W;
+    const int ntx = (t.B->ix1 - t.B->ix0 + TX - 1) / TX, nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
     const int tx = (int)(local % ntx);
     const long long rest = local / ntx;
     const int ty = (int)(rest % nty), tz = (int)(rest / nty);
-    t.i0 = t.B->ix0 + tx * 31 * W;
+    t.i0 = t.B->ix0 + tx * TX;
     t.j0 = t.B->iy0 + ty * TY;
-    t.kb = 1 + tz * plan.zseg;
-    t.ke = min(t.kb + plan.zseg, t.B->nz);
-    t.kstart = t.kb >= 2 ? t.kb - 1 : t.kb;
+    const int zs = plan.zseg, iz0 = t.B->iz0, iz1 = t.B->iz1;
+    if (!ZP) {
+        t.kb = iz0 + tz * zs;
+        t.ke = min(t.kb + zs, iz1);
+        t.kstart = t.kb - 1 >= iz0 ? t.kb - 1 : t.kb;
+    } else {
+        const int nlo = (iz0 - 1 + zs - 1) / zs;
+        if (tz < nlo) {
+            t.kb = 1 + tz * zs;
+            t.ke = min(t.kb + zs, iz0);
+        } else {
+            t.kb = max(iz1, iz0) + (tz - nlo) * zs;
+            t.ke = min(t.kb + zs, t.B->nz);
+        }
+        t.kstart = t.kb >= 2 ? t.kb - 1 : t.kb;
+    }
     return t;
 }
 
 // Fused H+E kernel over the fused region, fed by TMA, warp-specialised.
 // Warps 0..W-1 compute; warp W (one lane) is the producer, streaming planes
 // kstart..ke of the tile into an NS-stage ring (E^n with a one-node halo,
-// H~^{n-1/2} with the low halo row and column, coefficient ids), each stage
-// with a "full" mbarrier (TMA bytes) and an "empty" one (one arrival per
-// compute warp).  Compute warp w owns a strip of 31 columns: lane l sits on
-// column i0-1+31w+l, lane 0 being the strip's low-x halo.  Per plane k a lane
-// marches the tile's rows in y: it forms H~^{n+1/2}(k) at its column for the
-// halo row j0-1 and then row by row, so H(j-1) is already in registers, takes
-// H(i-1) from the lane to its left with a shuffle, and updates E^{n+1}(k).
-// H~ of halo nodes outside the fused region is read from the slab kernel's
+// H~^{n-1/2} with the low halo row and column, coefficient ids, and in the
+// z-UPML kernel the B~/D~ auxiliaries of z-UPML planes), each stage with a
+// "full" mbarrier (TMA bytes) and an "empty" one (one arrival per compute
+// warp).  Compute warp w owns 62 columns [i0 + 62w, i0 + 62w + 62); lane l
+// holds the column pair (g + 2l, g + 2l + 1), g = (i0 + 62w - 1) & ~1, so
+// one lane's loads and stores are 8 bytes and its arithmetic is paired FP32
+// (FFMA2/FMUL2).  Per plane k a lane marches the tile's rows in y: it forms
+// H~^{n+1/2}(k) at its two columns for the halo row j0-1 and then row by
+// row, so H(j-1) is already in registers; H(i-1) of its first column comes
+// from the lane to its left with a shuffle; then it updates E^{n+1}(k).  H~
+// of halo nodes outside the fused region is read from the slab kernel's
 // output instead.  The plane below the segment is run once for the tile's
-// H~x, H~y there; the plane above is read for E only.  In z-UPML planes
-// (sigma_z only) H~y, H~z carry B~y, B~z and E_y, E_z carry D~y, D~z.
-template <typename T, int TY, int W, int NS>
-__global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan)
+// H~x, H~y there (or read, see decode_tile); the plane above is read for E
+// only.  In z-UPML planes (sigma_z only) H~y, H~z carry B~y, B~z and E_y,
+// E_z carry D~y, D~z; those planes use the scalar update helpers per
+// element, every other plane the paired form, with identical rounding.
+template <typename T, int TY, int W, int NS, bool ZP>
+__global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::MINB)) k_fused(Plan plan)
 {
-    using St = Stage<T, TY, W>;
-    using L = FusedLayout<T, TY, W, NS>;
+    using St = Stage<T, TY, W, ZP>;
+    using L = FusedLayout<T, TY, W, NS, ZP>;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
     uint64_t *empty = full + NS;
@@ -317,15 +406,17 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
                 eph ^= 1u << s;
             }
         };
+        const long long n_items = ZP ? plan.n_zp : plan.n_int;
         for (;;) {
-            const long long item = atomicAdd(plan.work, 1);
-            if (item >= plan.n_int) break;
-            const Tile t = decode_tile<TY, W>(plan, item);
+            const long long item = atomicAdd(plan.work + (ZP ? 1 : 0), 1);
+            if (item >= n_items) break;
+            const Tile t = decode_tile<TY, W, ZP>(plan, item);
             const Board *B = t.B;
             const CUtensorMap *tm = B->tm;
             const int id16 = B->id16;
             const int xe0 = (t.i0 - 1) & ~7;
             const int xc0 = id16 ? (t.i0 & ~7) : (t.i0 & ~15);
+            const int xa0 = ((((t.i0 - 1) & ~1) - B->ix0)) & ~3;   // aux boxes: x relative to ix0
             const int last = t.ok ? t.ke : t.kstart;    // inactive board: one empty plane
             for (int p = t.kstart; p <= last; ++p, ++q, s = (s + 1 == NS ? 0 : s + 1)) {
                 acquire();
@@ -336,8 +427,10 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
                     continue;
                 }
                 const bool e_only = (p == t.ke);
+                const int zb = ZP && !e_only ? (p < B->iz0 ? 1 : (p >= B->iz1 ? 2 : 0)) : 0;
                 uint32_t bytes = St::E_BYTES;
                 if (!e_only) bytes += St::H_BYTES + (id16 ? St::C16_BYTES : St::C8_BYTES);
+                if (zb) bytes += St::A_BYTES;
                 mbar_expect_tx(&full[s], bytes);
                 for (int c = 0; c < 3; ++c)
                     tma_load_3d(st + St::E_OFF + c * St::E_CS * St::ES, tm + tm_e(t.par, c), xe0, t.j0 - 1, p, &full[s]);
@@ -346,6 +439,15 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
                         tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tm_h(t.par, c), xe0, t.j0 - 1, p,
                                     &full[s]);
                     tma_load_3d(st + St::C_OFF, tm + kTmCid, xc0, t.j0, p, &full[s]);
+                }
+                if (zb) {
+                    const int bx = zb - 1, kz = p - (zb == 1 ? 1 : B->iz1);
+                    unsigned char *a = st + St::A_OFF;
+                    tma_load_3d(a, tm + tm_zb(bx, 0, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
+                    tma_load_3d(a + St::B_CS * 4, tm + tm_zb(bx, 1, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
+                    tma_load_3d(a + 2 * St::B_CS * 4, tm + tm_zd(bx, 0), xa0, t.j0 - B->iy0, kz, &full[s]);
+                    tma_load_3d(a + 2 * St::B_CS * 4 + St::D_CS * 4, tm + tm_zd(bx, 1), xa0, t.j0 - B->iy0, kz,
+                                &full[s]);
                 }
             }
         }
@@ -362,7 +464,7 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
         mbar_wait(&full[sq], (fph >> sq) & 1u, plan.boards[0]->status, abort_flag);
         const long long item = *reinterpret_cast<volatile long long *>(smem + sq * St::BYTES + St::ITEM_OFF);
         if (item < 0) break;   // -1: no more work (the stage is left full)
-        const Tile t = decode_tile<TY, W>(plan, item);
+        const Tile t = decode_tile<TY, W, ZP>(plan, item);
         if (!t.ok) {           // one empty plane was sent for an inactive board
             fph ^= 1u << sq;
             __syncwarp();
@@ -375,65 +477,45 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
         const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0, iz1 = B->iz1;
         const int X = B->pitch;
         const long long P = B->plane, NN = B->nodes;
-        const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
+        const float2 Sx2 = make_float2(B->S[0], B->S[0]), Sy2 = make_float2(B->S[1], B->S[1]);
+        const float2 Sz2 = make_float2(B->S[2], B->S[2]);
+        const float2 nSx2 = make_float2(-B->S[0], -B->S[0]), nSy2 = make_float2(-B->S[1], -B->S[1]);
+        const float2 nSz2 = make_float2(-B->S[2], -B->S[2]);
         const int id16 = B->id16;
         const float4 *__restrict__ ctab = B->ctab;
         int *const status = B->status;
-        const int c = i0 - 1 + 31 * wy + lx;                  // this lane's column
-        const bool own_col = (lx > 0) && (c < ix1);
-        const bool col_slab = (c < ix0);                      // only lane 0 of warp 0 can be outside
+        const int wlo = i0 + kWarpCols * wy;               // first column the warp owns
+        const int whi = min(wlo + kWarpCols, ix1);
+        const int g = (wlo - 1) & ~1;
+        const int ca = g + 2 * lx, cb = ca + 1;            // this lane's columns
+        const bool own_a = ca >= wlo && ca < whi, own_b = cb >= wlo && cb < whi;
+        const bool slab_a = ca < ix0, slab_b = cb < ix0;  // halo column outside the fused region
+        const int ecol = (g - ((i0 - 1) & ~7)) + 2 * lx;   // column of ca in the E/H boxes (even)
+        const int xc0 = id16 ? (i0 & ~7) : (i0 & ~15);
+        const int ida = max(ca - xc0, 0), idb = cb - xc0;  // columns in the id box (clamped into it)
         const bool row_slab = (j0 - 1 < iy0);
-        const int ecol = ((i0 - 1) & 7) + 31 * wy + lx;       // column in the E/H boxes
-        const int ccol = (i0 - (id16 ? (i0 & ~7) : (i0 & ~15))) - 1 + 31 * wy + lx;   // in the id box
-        // global element (c, j0-1, kstart) in the output parity, advanced by P per plane
-        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(j0 - 1) * X + c);
+        // element (ca, j0-1, kstart) of component 0 in the output parity, advanced by P per plane
+        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(j0 - 1) * X + ca);
         const int zrow = B->zpitch;
         const long long zplane = (long long)(iy1 - iy0) * zrow;
-        const long long zcol = (long long)(j0 - 1 - iy0) * zrow + (c - ix0);   // aux of (c, j0-1)
+        const long long zcol = (long long)(j0 - iy0) * zrow + (ca - ix0);   // aux index of (ca, j0) in a plane
+        const int acol = (ca - ix0) - ((((i0 - 1) & ~1) - ix0) & ~3);       // column of ca in the aux boxes
         int s0 = sq, s1 = sq + 1 == NS ? 0 : sq + 1;
-        // z-UPML auxiliaries of this lane's column, fetched one plane ahead:
-        // B~y, B~z for box rows 0..TY (halo row and the tile rows), D~y, D~z
-        // for the tile rows
-        struct Aux {
-            float by[TY + 1], bz[TY + 1], dy[TY], dz[TY];
-        };
-        auto fetch_aux = [&](int k, Aux &a) {
-            const int zb = k < iz0 ? 1 : (k >= iz1 ? 2 : 0);
-            if (!zb) return;
-            const long long base = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
-            const float *by = B->zB[zb - 1][0][par], *bz = B->zB[zb - 1][1][par];
-            const float *dy = B->zD[zb - 1][0], *dz = B->zD[zb - 1][1];
-            const bool cin = !col_slab && c < ix1;
-#pragma unroll
-            for (int rr = 0; rr <= TY; ++rr) {
-                const int j = j0 - 1 + rr;
-                if (cin && j >= iy0 && j < iy1) {
-                    const long long x = base + (long long)rr * zrow;
-                    a.by[rr] = __ldg(by + x);
-                    a.bz[rr] = __ldg(bz + x);
-                    if (rr > 0 && lx > 0) { a.dy[rr - 1] = dy[x]; a.dz[rr - 1] = dz[x]; }
-                }
-            }
-        };
-        Aux ax, axn;
-        fetch_aux(kstart, ax);
 
-        float hk1x[TY], hk1y[TY];   // H~x, H~y of the previous plane, per row
+        float2 hk1x[TY], hk1y[TY];   // H~x, H~y of the previous plane, per row
 #pragma unroll
-        for (int r = 0; r < TY; ++r) { hk1x[r] = 0.f; hk1y[r] = 0.f; }
-        if (kstart == kb) {        // plane kb-1 is an outer z plane: read its H~
+        for (int r = 0; r < TY; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
+        if (kstart == kb) {         // plane kb-1 is not recomputed: read its H~
 #pragma unroll
             for (int r = 0; r < TY; ++r)
-                if (own_col && j0 + r < iy1) {
-                    const T *g = gp - P + (long long)(r + 1) * X;
-                    hk1x[r] = Io<T>::ld(g + 3 * NN);
-                    hk1y[r] = Io<T>::ld(g + 4 * NN);
+                if (j0 + r < iy1) {
+                    const T *gq = gp - P + (long long)(r + 1) * X;
+                    if (own_a) { hk1x[r].x = Io<T>::ld(gq + 3 * NN); hk1y[r].x = Io<T>::ld(gq + 4 * NN); }
+                    if (own_b) { hk1x[r].y = Io<T>::ld(gq + 3 * NN + 1); hk1y[r].y = Io<T>::ld(gq + 4 * NN + 1); }
                 }
         }
         fph ^= 1u << s0;     // the item's first plane was waited for above
-        (void)status;
         for (int k = kstart; k < ke; ++k, gp += P) {
-            if (k + 1 < ke) fetch_aux(k + 1, axn);
             mbar_wait(&full[s1], (fph >> s1) & 1u, status, abort_flag);
             fph ^= 1u << s1;
             const unsigned char *st0 = smem + s0 * St::BYTES, *st1 = smem + s1 * St::BYTES;
@@ -441,12 +523,14 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
             const T *E1 = reinterpret_cast<const T *>(st1 + St::E_OFF) + ecol;
             const T *H0 = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol;
             const unsigned char *C0 = st0 + St::C_OFF;
+            const float *A0 = reinterpret_cast<const float *>(st0 + St::A_OFF) + acol;
             constexpr int EW = St::EW, HW = St::HW, ECS = St::E_CS, HCS = St::H_CS;
-            const int zb = k < iz0 ? 1 : (k >= iz1 ? 2 : 0);
+            constexpr int AW = St::AW, BCS = St::B_CS, DCS = St::D_CS;
+            const int zb = ZP ? (k < iz0 ? 1 : (k >= iz1 ? 2 : 0)) : 0;
             ZCoef z;
             float *zdy = nullptr, *zdz = nullptr, *nzby = nullptr, *nzbz = nullptr;
             long long za = 0;
-            if (zb) {
+            if (ZP && zb) {
                 z.zi = B->cw[2][0][k];
                 z.zh = B->cw[2][1][k];
                 za = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
@@ -454,91 +538,129 @@ __global__ void __launch_bounds__(32 * W + 32, W == 4 ? 2 : 4) k_fused(Plan plan
                 zdy = B->zD[zb - 1][0]; zdz = B->zD[zb - 1][1];
             }
             const bool full_plane = k >= kb;
-            // H~^{n+1/2}(k) at (c, j0-1+rr) from box row rr; Bo/Bn: B~y, B~z
-            auto hnode = [&](int rr, bool in_f, float &hx, float &hy, float &hz, float &nby, float &nbz) {
-                const float ezr = cvt<T>(E0[2 * ECS + rr * EW]), ezu = cvt<T>(E0[2 * ECS + (rr + 1) * EW]);
-                const float eyr = cvt<T>(E0[ECS + rr * EW]), eyk = cvt<T>(E1[ECS + rr * EW]);
-                const float exr = cvt<T>(E0[rr * EW]), exk = cvt<T>(E1[rr * EW]), exu = cvt<T>(E0[(rr + 1) * EW]);
-                const float ezx = cvt<T>(E0[2 * ECS + rr * EW + 1]), eyx = cvt<T>(E0[ECS + rr * EW + 1]);
-                const float scx = curl2(ezu, ezr, eyk, eyr, Sy, Sz);
-                const float scy = curl2(exk, exr, ezx, ezr, Sz, Sx);
-                const float scz = curl2(eyx, eyr, exu, exr, Sx, Sy);
-                const float Boy = (zb && in_f) ? ax.by[rr] : 0.f;
-                const float Boz = (zb && in_f) ? ax.bz[rr] : 0.f;
-                hx = fused_hx(cvt<T>(H0[rr * HW]), scx, zb, z);
-                hy = fused_hy(cvt<T>(H0[HCS + rr * HW]), scy, zb, z, Boy, nby);
-                hz = fused_hz(cvt<T>(H0[2 * HCS + rr * HW]), scz, zb, z, Boz, nbz);
+            // coefficient rows of the lane's two nodes (ids clamped into the box,
+            // so every lookup is a valid row)
+            float4 cea[TY], ceb[TY];
+#pragma unroll
+            for (int r = 0; r < TY; ++r) {
+                const int ia = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + ida]
+                                    : (int)C0[r * St::C8W + ida];
+                const int ib = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + idb]
+                                    : (int)C0[r * St::C8W + idb];
+                cea[r] = __ldg(ctab + ia);
+                ceb[r] = __ldg(ctab + ib);
+            }
+            // E^n at box row rr (own node), and H~^{n+1/2}(k) there from the staged planes
+            auto hrow = [&](int rr, bool in_f, float2 &ex, float2 &ey, float2 &ez, float2 &hx, float2 &hy, float2 &hz,
+                            float2 &nby, float2 &nbz) {
+                ez = Pair<T>::lds(E0 + 2 * ECS + rr * EW);
+                ey = Pair<T>::lds(E0 + ECS + rr * EW);
+                ex = Pair<T>::lds(E0 + rr * EW);
+                const float2 ezu = Pair<T>::lds(E0 + 2 * ECS + (rr + 1) * EW);
+                const float2 exu = Pair<T>::lds(E0 + (rr + 1) * EW);
+                const float2 eyk = Pair<T>::lds(E1 + ECS + rr * EW), exk = Pair<T>::lds(E1 + rr * EW);
+                const float ez2 = cvt<T>(E0[2 * ECS + rr * EW + 2]), ey2 = cvt<T>(E0[ECS + rr * EW + 2]);
+                const float2 ezx = make_float2(ez.y, ez2), eyx = make_float2(ey.y, ey2);   // E at (c+1)
+                const float2 scx = curl2v(ezu, ez, eyk, ey, Sy2, nSz2);
+                const float2 scy = curl2v(exk, ex, ezx, ez, Sz2, nSx2);
+                const float2 scz = curl2v(eyx, ey, exu, ex, Sx2, nSy2);
+                const float2 ohx = Pair<T>::lds(H0 + rr * HW), ohy = Pair<T>::lds(H0 + HCS + rr * HW);
+                const float2 ohz = Pair<T>::lds(H0 + 2 * HCS + rr * HW);
+                if (!ZP || !zb) {
+                    hx = sub2(ohx, scx);
+                    hy = sub2(ohy, scy);
+                    hz = sub2(ohz, scz);
+                } else {
+                    // B~ of the node: box row rr; zero outside the fused rows
+                    float2 boy = make_float2(A0[rr * AW], A0[rr * AW + 1]);
+                    float2 boz = make_float2(A0[BCS + rr * AW], A0[BCS + rr * AW + 1]);
+                    if (!in_f) boy = boz = make_float2(0.f, 0.f);
+                    hx.x = fused_hx(ohx.x, scx.x, zb, z);
+                    hx.y = fused_hx(ohx.y, scx.y, zb, z);
+                    hy.x = fused_hy(ohy.x, scy.x, zb, z, boy.x, nby.x);
+                    hy.y = fused_hy(ohy.y, scy.y, zb, z, boy.y, nby.y);
+                    hz.x = fused_hz(ohz.x, scz.x, zb, z, boz.x, nbz.x);
+                    hz.y = fused_hz(ohz.y, scz.y, zb, z, boz.y, nbz.y);
+                }
+            };
+            // halo elements outside the fused region come from the slab output
+            auto slab_fix = [&](int rr, float2 &hx, float2 &hy, float2 &hz) {
+                if (j0 - 1 + rr >= iy1) return;
+                const T *gq = gp + (long long)rr * X;
+                if (slab_a) { hx.x = Io<T>::ld(gq + 3 * NN); hy.x = Io<T>::ld(gq + 4 * NN); hz.x = Io<T>::ld(gq + 5 * NN); }
+                if (slab_b) {
+                    hx.y = Io<T>::ld(gq + 3 * NN + 1); hy.y = Io<T>::ld(gq + 4 * NN + 1); hz.y = Io<T>::ld(gq + 5 * NN + 1);
+                }
             };
 
-            float4 ce[TY];   // coefficient rows of the lane's nodes, fetched first
-#pragma unroll
-            for (int r = 0; r < TY; ++r) {
-                ce[r] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (full_plane && own_col && j0 + r < iy1) {
-                    const int id = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + ccol]
-                                        : (int)C0[r * St::C8W + ccol];
-                    ce[r] = __ldg(ctab + id);
-                }
-            }
-            float px = 0.f, py = 0.f, pz = 0.f;   // H~ at (c, j-1)
+            float2 px = make_float2(0.f, 0.f), pz = px;   // H~x, H~z at (., j-1)
             if (full_plane) {
-                float d0, d1;
-                if (row_slab || col_slab) {
-                    const T *g = gp;
-                    px = Io<T>::ld(g + 3 * NN); py = Io<T>::ld(g + 4 * NN); pz = Io<T>::ld(g + 5 * NN);
+                if (row_slab) {   // row j0-1 lies in the low-y slab: read its H~ (own columns)
+                    if (own_a && own_b) {
+                        px = Pair<T>::ldg(gp + 3 * NN);
+                        pz = Pair<T>::ldg(gp + 5 * NN);
+                    } else if (own_a) {
+                        px.x = Io<T>::ld(gp + 3 * NN);
+                        pz.x = Io<T>::ld(gp + 5 * NN);
+                    } else if (own_b) {
+                        px.y = Io<T>::ld(gp + 3 * NN + 1);
+                        pz.y = Io<T>::ld(gp + 5 * NN + 1);
+                    }
                 } else {
-                    hnode(0, true, px, py, pz, d0, d1);
+                    float2 ex, ey, ez, hy, d0, d1;
+                    hrow(0, true, ex, ey, ez, px, hy, pz, d0, d1);
+                    slab_fix(0, px, hy, pz);
                 }
             }
 #pragma unroll
             for (int r = 0; r < TY; ++r) {
-                const int j = j0 + r;
-                float hx, hy, hz, nby = 0.f, nbz = 0.f;
-                if (col_slab) {
-                    const T *g = gp + (long long)(r + 1) * X;
-                    hx = Io<T>::ld(g + 3 * NN); hy = Io<T>::ld(g + 4 * NN); hz = Io<T>::ld(g + 5 * NN);
-                } else {
-                    hnode(r + 1, j < iy1, hx, hy, hz, nby, nbz);
-                }
-                const float hyl = __shfl_up_sync(0xffffffffu, hy, 1);   // H~ at (c-1, j)
-                const float hzl = __shfl_up_sync(0xffffffffu, hz, 1);
-                if (full_plane && own_col && j < iy1) {
-                    const int rr = r + 1;
-                    const float4 cr = ce[r];
-                    const float scx = curl2(hz, pz, hy, hk1y[r], Sy, Sz);
-                    const float scy = curl2(hx, hk1x[r], hz, hzl, Sz, Sx);
-                    const float scz = curl2(hy, hyl, hx, px, Sx, Sy);
-                    const float exo = cvt<T>(E0[rr * EW]), eyo = cvt<T>(E0[ECS + rr * EW]), ezo = cvt<T>(E0[2 * ECS + rr * EW]);
-                    float exv, eyv, ezv;
+                const int j = j0 + r, rr = r + 1;
+                float2 ex, ey, ez, hx, hy, hz, nby = make_float2(0.f, 0.f), nbz = nby;
+                hrow(rr, j < iy1, ex, ey, ez, hx, hy, hz, nby, nbz);
+                slab_fix(rr, hx, hy, hz);
+                const float hyl = __shfl_up_sync(0xffffffffu, hy.y, 1);   // H~ at (ca-1, j)
+                const float hzl = __shfl_up_sync(0xffffffffu, hz.y, 1);
+                if (full_plane && j < iy1) {
+                    const float2 hym = make_float2(hyl, hy.x), hzm = make_float2(hzl, hz.x);   // H~ at (c-1, j)
+                    const float2 scx = curl2v(hz, pz, hy, hk1y[r], Sy2, nSz2);
+                    const float2 scy = curl2v(hx, hk1x[r], hz, hzm, Sz2, nSx2);
+                    const float2 scz = curl2v(hy, hym, hx, px, Sx2, nSy2);
+                    float2 exv, eyv, ezv;
                     T *o = gp + (long long)rr * X;
-                    if (!zb) {
-                        exv = __fmaf_rn(cr.x, scx, exo);
-                        eyv = __fmaf_rn(cr.y, scy, eyo);
-                        ezv = __fmaf_rn(cr.z, scz, ezo);
+                    if (!ZP || !zb) {
+                        exv = make_float2(__fmaf_rn(cea[r].x, scx.x, ex.x), __fmaf_rn(ceb[r].x, scx.y, ex.y));
+                        eyv = make_float2(__fmaf_rn(cea[r].y, scy.x, ey.x), __fmaf_rn(ceb[r].y, scy.y, ey.y));
+                        ezv = make_float2(__fmaf_rn(cea[r].z, scz.x, ez.x), __fmaf_rn(ceb[r].z, scz.y, ez.y));
                     } else {
-                        const long long a = za + (long long)rr * zrow;
-                        float nd, ndy, ndz;
-                        exv = upml_e2(exo, scx, cr.x, kOne, z.zi, kOne, false, 0.f, nd);
-                        eyv = upml_e2(eyo, scy, cr.y, z.zi, kOne, kOne, true, ax.dy[r], ndy);
-                        ezv = upml_e2(ezo, scz, cr.z, kOne, kOne, z.zh, true, ax.dz[r], ndz);
-                        zdy[a] = ndy;
-                        zdz[a] = ndz;
-                        nzby[a] = nby;
-                        nzbz[a] = nbz;
+                        const long long a = za + (long long)r * zrow;
+                        const float *dyo = A0 + 2 * BCS + r * AW, *dzo = dyo + DCS;
+                        float nd;
+                        float2 ndy, ndz;
+                        exv.x = upml_e2(ex.x, scx.x, cea[r].x, kOne, z.zi, kOne, false, 0.f, nd);
+                        exv.y = upml_e2(ex.y, scx.y, ceb[r].x, kOne, z.zi, kOne, false, 0.f, nd);
+                        eyv.x = upml_e2(ey.x, scy.x, cea[r].y, z.zi, kOne, kOne, true, dyo[0], ndy.x);
+                        eyv.y = upml_e2(ey.y, scy.y, ceb[r].y, z.zi, kOne, kOne, true, dyo[1], ndy.y);
+                        ezv.x = upml_e2(ez.x, scz.x, cea[r].z, kOne, kOne, z.zh, true, dzo[0], ndz.x);
+                        ezv.y = upml_e2(ez.y, scz.y, ceb[r].z, kOne, kOne, z.zh, true, dzo[1], ndz.y);
+                        if (own_a) { zdy[a] = ndy.x; zdz[a] = ndz.x; nzby[a] = nby.x; nzbz[a] = nbz.x; }
+                        if (own_b) { zdy[a + 1] = ndy.y; zdz[a + 1] = ndz.y; nzby[a + 1] = nby.y; nzbz[a + 1] = nbz.y; }
                     }
-                    Io<T>::st(o + 3 * NN, hx);
-                    Io<T>::st(o + 4 * NN, hy);
-                    Io<T>::st(o + 5 * NN, hz);
-                    Io<T>::st(o, exv);
-                    Io<T>::st(o + NN, eyv);
-                    Io<T>::st(o + 2 * NN, ezv);
+                    if (own_a && own_b) {
+                        Pair<T>::st(o + 3 * NN, hx); Pair<T>::st(o + 4 * NN, hy); Pair<T>::st(o + 5 * NN, hz);
+                        Pair<T>::st(o, exv); Pair<T>::st(o + NN, eyv); Pair<T>::st(o + 2 * NN, ezv);
+                    } else if (own_a) {
+                        Io<T>::st(o + 3 * NN, hx.x); Io<T>::st(o + 4 * NN, hy.x); Io<T>::st(o + 5 * NN, hz.x);
+                        Io<T>::st(o, exv.x); Io<T>::st(o + NN, eyv.x); Io<T>::st(o + 2 * NN, ezv.x);
+                    } else if (own_b) {
+                        Io<T>::st(o + 3 * NN + 1, hx.y); Io<T>::st(o + 4 * NN + 1, hy.y); Io<T>::st(o + 5 * NN + 1, hz.y);
+                        Io<T>::st(o + 1, exv.y); Io<T>::st(o + NN + 1, eyv.y); Io<T>::st(o + 2 * NN + 1, ezv.y);
+                    }
                 }
                 hk1x[r] = hx;
                 hk1y[r] = hy;
-                px = hx; py = hy; pz = hz;
+                px = hx;
+                pz = hz;
             }
-            (void)py;
-            ax = axn;
             __syncwarp();
             if (lx == 0) mbar_arrive(&empty[s0]);
             s0 = s1;
@@ -889,16 +1011,14 @@ __global__ void k_energy_final(const double *partials, int n, double *out2)
 }
 
 // ------------------------------------------------------------------ launchers
-// Fused-kernel configurations: W compute warps x 31 columns by TY rows.
-template <int TY, int W>
-struct FusedTune {
-    static constexpr int NS = 4;
-};
+// Fused-kernel configurations: W compute warps x 62 columns by TY rows, an
+// NS-stage ring; ZP selects the z-UPML launch.
+constexpr int kFusedStages = 3;
 
-template <typename T, int TY, int W>
+template <typename T, int TY, int W, bool ZP>
 struct FusedCfg {
-    static constexpr int NS = FusedTune<TY, W>::NS;
-    using L = FusedLayout<T, TY, W, NS>;
+    static constexpr int NS = kFusedStages;
+    using L = FusedLayout<T, TY, W, NS, ZP>;
     static dim3 block() { return dim3(32, W + 1); }
     static int grid()
     {
@@ -907,33 +1027,34 @@ struct FusedCfg {
             int dev = 0, sms = 0, per = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS>, 32 * (W + 1), L::BYTES);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS, ZP>, 32 * (W + 1), L::BYTES);
             g = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
         }
         return g;
     }
     static cudaError_t set_limit()
     {
-        return cudaFuncSetAttribute(k_fused<T, TY, W, NS>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+        return cudaFuncSetAttribute(k_fused<T, TY, W, NS, ZP>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
     }
     static void launch(const Plan &plan, cudaStream_t st)
     {
-        const int g = (int)(plan.n_int < grid() ? plan.n_int : grid());
-        cudaMemsetAsync(plan.work, 0, sizeof(int), st);
-        k_fused<T, TY, W, NS><<<g, block(), L::BYTES, st>>>(plan);
+        const long long n = ZP ? plan.n_zp : plan.n_int;
+        if (n <= 0) return;
+        const int g = (int)(n < grid() ? n : grid());
+        k_fused<T, TY, W, NS, ZP><<<g, block(), L::BYTES, st>>>(plan);
     }
 };
 
 // Supported fused tiles (tile_x columns x tile_y rows): 62x4, 62x8, 124x4, 124x8.
-template <typename T>
+template <typename T, bool ZP>
 static void launch_fused(const Plan &plan, cudaStream_t st)
 {
     const int key = plan.tile_x * 16 + plan.tile_y;
     switch (key) {
-    case 62 * 16 + 4: FusedCfg<T, 4, 2>::launch(plan, st); break;
-    case 62 * 16 + 8: FusedCfg<T, 8, 2>::launch(plan, st); break;
-    case 124 * 16 + 8: FusedCfg<T, 8, 4>::launch(plan, st); break;
-    default: FusedCfg<T, 4, 4>::launch(plan, st); break;
+    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP>::launch(plan, st); break;
+    case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP>::launch(plan, st); break;
+    case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP>::launch(plan, st); break;
+    default: FusedCfg<T, 4, 1, ZP>::launch(plan, st); break;
     }
 }
 
@@ -945,8 +1066,17 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
         if (plan.n_slab > 0)
             k_slab_h<T><<<(int)(plan.n_slab < grid_cap ? plan.n_slab : grid_cap), kSlabThreads, 0, st>>>(plan);
         break;
+    case kPhaseFusedZ:
+        if (plan.n_zp > 0) {
+            cudaMemsetAsync(plan.work + 1, 0, sizeof(int), st);
+            launch_fused<T, true>(plan, st);
+        }
+        break;
     case kPhaseInterior:
-        if (plan.n_int > 0) launch_fused<T>(plan, st);
+        if (plan.n_int > 0) {
+            cudaMemsetAsync(plan.work, 0, sizeof(int), st);
+            launch_fused<T, false>(plan, st);
+        }
         break;
     case kPhaseSlabE:
         if (plan.n_slab > 0)
@@ -982,8 +1112,10 @@ bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (t
 template <typename T>
 static cudaError_t limits_t()
 {
-    cudaError_t e[4] = {FusedCfg<T, 4, 2>::set_limit(), FusedCfg<T, 8, 2>::set_limit(), FusedCfg<T, 4, 4>::set_limit(),
-                        FusedCfg<T, 8, 4>::set_limit()};
+    cudaError_t e[8] = {FusedCfg<T, 4, 1, false>::set_limit(), FusedCfg<T, 8, 1, false>::set_limit(),
+                        FusedCfg<T, 4, 2, false>::set_limit(), FusedCfg<T, 8, 2, false>::set_limit(),
+                        FusedCfg<T, 4, 1, true>::set_limit(),  FusedCfg<T, 8, 1, true>::set_limit(),
+                        FusedCfg<T, 4, 2, true>::set_limit(),  FusedCfg<T, 8, 2, true>::set_limit()};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;

@@ -65,9 +65,10 @@ class Solver:
         return self
 
     def step_profiled(self, n: int) -> np.ndarray:
-        """n steps with per-phase CUDA-event timing: [slab H, interior, slab E,
-        sources/probes, DFT] summed device milliseconds."""
-        ms = (ctypes.c_double * 5)()
+        """n steps with per-phase CUDA-event timing: [slab H, fused z-UPML,
+        fused interior, slab E, sources/probes, DFT] summed device
+        milliseconds."""
+        ms = (ctypes.c_double * 6)()
         C.fdtd_step_profiled(self.ctx, int(n), ms)
         return np.array(list(ms))
 
