@@ -790,7 +790,8 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
         sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
         sl.block0 = blocks;
-        blocks += (int)((sl.n + kSlabThreads - 1) / kSlabThreads);
+        const long long cols = (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
+        blocks += (int)((cols + kSlabThreads - 1) / kSlabThreads);
         const int lo[3] = {sl.i0, sl.j0, sl.k0}, hi[3] = {sl.i1, sl.j1, sl.k1};
         auto any_nontrivial = [&](int axis, int half, bool need_b1g, bool need_apam) {
             for (int t = lo[axis]; t < hi[axis]; ++t) {

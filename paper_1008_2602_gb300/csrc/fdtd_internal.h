@@ -54,6 +54,7 @@ struct Slab {
     int ni, nj;                   // i1 - i0, j1 - j0
     long long n;                  // nodes in the box
     long long block0;             // first slab-kernel block of this slab (board-local)
+                                  // (blocks cover ni * nj * ceil(nk / kSlabKz) threads)
     float *aux[6];                // D~x, D~y, D~z, B~x, B~y, B~z or nullptr
 };
 
@@ -145,6 +146,7 @@ __host__ __device__ constexpr int box_c16(int tx) { return box_up(tx + 7, 8); }
 __host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 5, 4); }
 
 constexpr int kSlabThreads = 256;
+constexpr int kSlabKz = 4;          // planes per slab-kernel thread
 constexpr int kDftProbeGroup = 4;
 
 enum Phase : int { kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseInterior = 2, kPhaseSlabE = 3, kPhasePost = 4, kNumPhases = 5 };

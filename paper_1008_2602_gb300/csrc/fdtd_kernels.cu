@@ -241,6 +241,40 @@ struct Pair<__nv_bfloat16> {
     }
 };
 
+// Stores of the fused kernel.  Written as global-space stores without a
+// compiler memory barrier, so the compiler knows they cannot alias the
+// shared-memory stages and may hoist the next row's shared loads above them.
+// (No value this kernel stores is read back by it.)
+__device__ __forceinline__ size_t gaddr(const void *p) { return __cvta_generic_to_global(p); }
+__device__ __forceinline__ void stg1(float *p, float v)
+{
+    asm volatile("st.global.f32 [%0], %1;" ::"l"(gaddr(p)), "f"(v));
+}
+__device__ __forceinline__ void stg1(__half *p, float v)
+{
+    const __half h = __float2half_rn(v);
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(gaddr(p)), "h"(*reinterpret_cast<const unsigned short *>(&h)));
+}
+__device__ __forceinline__ void stg1(__nv_bfloat16 *p, float v)
+{
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    asm volatile("st.global.b16 [%0], %1;" ::"l"(gaddr(p)), "h"(*reinterpret_cast<const unsigned short *>(&h)));
+}
+__device__ __forceinline__ void stg2(float *p, float2 v)
+{
+    asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(gaddr(p)), "f"(v.x), "f"(v.y));
+}
+__device__ __forceinline__ void stg2(__half *p, float2 v)
+{
+    const __half2 h = __float22half2_rn(v);
+    asm volatile("st.global.b32 [%0], %1;" ::"l"(gaddr(p)), "r"(*reinterpret_cast<const unsigned int *>(&h)));
+}
+__device__ __forceinline__ void stg2(__nv_bfloat16 *p, float2 v)
+{
+    const __nv_bfloat162 h = __float22bfloat162_rn(v);
+    asm volatile("st.global.b32 [%0], %1;" ::"l"(gaddr(p)), "r"(*reinterpret_cast<const unsigned int *>(&h)));
+}
+
 // Paired forms of curl2 and of h - s.  Per element they round exactly like
 // the scalar forms: a - b == fma(b, -1, a) (the product is exact), and
 // fma(-Sb, d, x) is the same single rounding either way.
@@ -278,9 +312,9 @@ struct Stage {
     static constexpr int E_OFF = 0;
     static constexpr int H_OFF = 3 * E_CS * ES;
     static constexpr int C_OFF = H_OFF + 3 * H_CS * ES;
-    static constexpr int A_OFF = C_OFF + al(C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES);
-    static constexpr int ITEM_OFF = A_OFF + (ZP ? 2 * (B_CS + D_CS) * 4 : 0);   // item id of the plane
-    static constexpr int BYTES = ITEM_OFF + 128;
+    static constexpr int ITEM_OFF = (C_OFF + (C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES) + 7) & ~7;   // item id
+    static constexpr int A_OFF = al(ITEM_OFF + 8);
+    static constexpr int BYTES = A_OFF + (ZP ? 2 * (B_CS + D_CS) * 4 : 0);
 };
 
 template <typename T, int TY, int W, int NS, bool ZP>
@@ -288,10 +322,10 @@ struct FusedLayout {
     using St = Stage<T, TY, W, ZP>;
     static constexpr int BAR_OFF = NS * St::BYTES;
     static constexpr int BYTES = BAR_OFF + 2 * NS * 8 + 16;
-    // blocks per SM that shared memory allows (228 KB per SM, 1 KB reserved
-    // per block); the register budget keeps them resident but never drops
+    // blocks per SM that shared memory allows (227 KB usable per SM, 1 KB
+    // reserved per block); the register budget keeps them resident but never drops
     // below 128 registers per thread (176 for 8-row tiles)
-    static constexpr int PER_SM = 233472 / (BYTES + 1024);
+    static constexpr int PER_SM = 232448 / (BYTES + 1024);
     static constexpr int REG_SM = 65536 / ((TY >= 8 ? 176 : 128) * (32 * W + 32));
     static constexpr int CAP = PER_SM < REG_SM ? PER_SM : REG_SM;
     static constexpr int MINB = CAP < 1 ? 1 : (CAP > 8 ? 8 : CAP);
@@ -642,18 +676,20 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                         eyv.y = upml_e2(ey.y, scy.y, ceb[r].y, z.zi, kOne, kOne, true, dyo[1], ndy.y);
                         ezv.x = upml_e2(ez.x, scz.x, cea[r].z, kOne, kOne, z.zh, true, dzo[0], ndz.x);
                         ezv.y = upml_e2(ez.y, scz.y, ceb[r].z, kOne, kOne, z.zh, true, dzo[1], ndz.y);
-                        if (own_a) { zdy[a] = ndy.x; zdz[a] = ndz.x; nzby[a] = nby.x; nzbz[a] = nbz.x; }
-                        if (own_b) { zdy[a + 1] = ndy.y; zdz[a + 1] = ndz.y; nzby[a + 1] = nby.y; nzbz[a + 1] = nbz.y; }
+                        if (own_a) { stg1(zdy + a, ndy.x); stg1(zdz + a, ndz.x); stg1(nzby + a, nby.x); stg1(nzbz + a, nbz.x); }
+                        if (own_b) {
+                            stg1(zdy + a + 1, ndy.y); stg1(zdz + a + 1, ndz.y); stg1(nzby + a + 1, nby.y); stg1(nzbz + a + 1, nbz.y);
+                        }
                     }
                     if (own_a && own_b) {
-                        Pair<T>::st(o + 3 * NN, hx); Pair<T>::st(o + 4 * NN, hy); Pair<T>::st(o + 5 * NN, hz);
-                        Pair<T>::st(o, exv); Pair<T>::st(o + NN, eyv); Pair<T>::st(o + 2 * NN, ezv);
+                        stg2(o + 3 * NN, hx); stg2(o + 4 * NN, hy); stg2(o + 5 * NN, hz);
+                        stg2(o, exv); stg2(o + NN, eyv); stg2(o + 2 * NN, ezv);
                     } else if (own_a) {
-                        Io<T>::st(o + 3 * NN, hx.x); Io<T>::st(o + 4 * NN, hy.x); Io<T>::st(o + 5 * NN, hz.x);
-                        Io<T>::st(o, exv.x); Io<T>::st(o + NN, eyv.x); Io<T>::st(o + 2 * NN, ezv.x);
+                        stg1(o + 3 * NN, hx.x); stg1(o + 4 * NN, hy.x); stg1(o + 5 * NN, hz.x);
+                        stg1(o, exv.x); stg1(o + NN, eyv.x); stg1(o + 2 * NN, ezv.x);
                     } else if (own_b) {
-                        Io<T>::st(o + 3 * NN + 1, hx.y); Io<T>::st(o + 4 * NN + 1, hy.y); Io<T>::st(o + 5 * NN + 1, hz.y);
-                        Io<T>::st(o + 1, exv.y); Io<T>::st(o + NN + 1, eyv.y); Io<T>::st(o + 2 * NN + 1, ezv.y);
+                        stg1(o + 3 * NN + 1, hx.y); stg1(o + 4 * NN + 1, hy.y); stg1(o + 5 * NN + 1, hz.y);
+                        stg1(o + 1, exv.y); stg1(o + NN + 1, eyv.y); stg1(o + 2 * NN + 1, ezv.y);
                     }
                 }
                 hk1x[r] = hx;
@@ -673,13 +709,17 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
 }
 
 // ------------------------------------------------------------------ slabs
-struct SlabPos {
+// A slab thread owns one (i, j) column of its slab for kSlabKz consecutive
+// planes: consecutive threads take consecutive i (coalesced rows), and the
+// per-column UPML factors and index arithmetic are paid once per column.
+struct SlabCol {
     const Slab *sl;
-    long long t;          // slab-local index (aux index)
-    int i, j, k;
+    long long t;          // slab-local (aux) index of (i, j, kbeg); + nij per plane
+    int nij;
+    int i, j, kbeg, kend;
 };
 
-__device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, const Board *&B, SlabPos &sp)
+__device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, const Board *&B, SlabCol &sc)
 {
     const int b = find_board(plan.slab_prefix, plan.nb, blk);
     B = plan.boards[b];
@@ -688,14 +728,19 @@ __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, con
     int s = 0;
     while (s + 1 < B->n_slab && B->slab[s + 1].block0 <= lb) ++s;
     const Slab *sl = &B->slab[s];
-    const long long t = (long long)(lb - sl->block0) * kSlabThreads + threadIdx.x;
-    if (t >= sl->n) return false;
-    sp.sl = sl;
-    sp.t = t;
-    sp.i = sl->i0 + (int)(t % sl->ni);
-    const long long r = t / sl->ni;
-    sp.j = sl->j0 + (int)(r % sl->nj);
-    sp.k = sl->k0 + (int)(r / sl->nj);
+    const int ni = sl->ni, nij = ni * sl->nj;
+    const int nkz = (sl->k1 - sl->k0 + kSlabKz - 1) / kSlabKz;
+    const int tt = (lb - (int)sl->block0) * kSlabThreads + (int)threadIdx.x;
+    if (tt >= nij * nkz) return false;
+    const int kz = tt / nij, ij = tt - kz * nij;
+    const int jj = ij / ni;
+    sc.sl = sl;
+    sc.nij = nij;
+    sc.i = sl->i0 + (ij - jj * ni);
+    sc.j = sl->j0 + jj;
+    sc.kbeg = sl->k0 + kz * kSlabKz;
+    sc.kend = min(sc.kbeg + kSlabKz, sl->k1);
+    sc.t = (long long)kz * kSlabKz * nij + ij;
     return true;
 }
 
@@ -727,101 +772,144 @@ __device__ __forceinline__ float upml_e(float e, float scurl, float ce, const Co
     return __fmaf_rn(__fmul_rn(ce, bb.g), scurl, __fmul_rn(bb.b1, e));
 }
 
+// The slab kernels issue every load of a node unconditionally, with the
+// offsets of neighbours that do not exist (i = nx, j = ny, k = nz, or the
+// image across an outer wall) clamped to an in-bounds node, so all of a
+// column's loads can be in flight together; only the stores are conditional.
 template <typename T>
 __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
 {
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
-        SlabPos sp;
-        if (!slab_locate(plan, blk, B, sp)) continue;
+        SlabCol sc;
+        if (!slab_locate(plan, blk, B, sc)) continue;
         const long long step = *((volatile long long *)B->step);
         const Fields<T> F(B, (int)(step & 1));
-        const int i = sp.i, j = sp.j, k = sp.k;
+        const int i = sc.i, j = sc.j, nz = B->nz;
         const int X = B->pitch;
         const long long P = B->plane;
-        const long long idx = (long long)k * P + (long long)j * X + i;
         const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
-        const Slab &sl = *sp.sl;
-        if (j < B->ny && k < B->nz) {   // H_x(i, j+1/2, k+1/2)
-            const float sc = curl2(Io<T>::ld(F.ez + idx + X), Io<T>::ld(F.ez + idx),
-                                   Io<T>::ld(F.ey + idx + P), Io<T>::ld(F.ey + idx), Sy, Sz);
-            const float h = upml_h(Io<T>::ld(F.hx + idx), sc, B->cw[1][1][j], B->cw[2][1][k], B->cw[0][0][i],
-                                   sl.aux[3], sp.t);
-            Io<T>::st(F.ohx + idx, h);
-        }
-        if (i < B->nx && k < B->nz) {   // H_y(i+1/2, j, k+1/2)
-            const float sc = curl2(Io<T>::ld(F.ex + idx + P), Io<T>::ld(F.ex + idx),
-                                   Io<T>::ld(F.ez + idx + 1), Io<T>::ld(F.ez + idx), Sz, Sx);
-            const float h = upml_h(Io<T>::ld(F.hy + idx), sc, B->cw[2][1][k], B->cw[0][1][i], B->cw[1][0][j],
-                                   sl.aux[4], sp.t);
-            Io<T>::st(F.ohy + idx, h);
-        }
-        if (i < B->nx && j < B->ny) {   // H_z(i+1/2, j+1/2, k)
-            const float sc = curl2(Io<T>::ld(F.ey + idx + 1), Io<T>::ld(F.ey + idx),
-                                   Io<T>::ld(F.ex + idx + X), Io<T>::ld(F.ex + idx), Sx, Sy);
-            const float h = upml_h(Io<T>::ld(F.hz + idx), sc, B->cw[0][1][i], B->cw[1][1][j], B->cw[2][0][k],
-                                   sl.aux[5], sp.t);
-            Io<T>::st(F.ohz + idx, h);
+        const Slab &sl = *sc.sl;
+        float *const ax = sl.aux[3], *const ay = sl.aux[4], *const az = sl.aux[5];
+        const bool xin = i < B->nx, yin = j < B->ny;
+        const int di = xin ? 1 : 0, dj = yin ? X : 0;   // clamped +x, +y neighbour offsets
+        // factors fixed along the column: H_x (y half, x integer), H_y (x half,
+        // y integer), H_z (x half, y half)
+        const Coef y1 = B->cw[1][1][j], x0 = B->cw[0][0][i], x1 = B->cw[0][1][i], y0 = B->cw[1][0][j];
+        long long idx = (long long)sc.kbeg * P + (long long)j * X + i;
+        long long t = sc.t;
+        // E_y, E_x of the current plane; the (k+1) loads become the next plane's
+        float eyc = Io<T>::ld(F.ey + idx);
+        float exc = Io<T>::ld(F.ex + idx);
+#pragma unroll
+        for (int m = 0; m < kSlabKz; ++m) {
+            const int k = sc.kbeg + m;
+            if (k >= sc.kend) break;
+            const bool zin = k < nz;
+            const long long dk = zin ? P : 0;
+            const float eyu = Io<T>::ld(F.ey + idx + dk), exu = Io<T>::ld(F.ex + idx + dk);
+            const float ezc = Io<T>::ld(F.ez + idx);
+            const float ezj = Io<T>::ld(F.ez + idx + dj), ezi = Io<T>::ld(F.ez + idx + di);
+            const float eyi = Io<T>::ld(F.ey + idx + di), exj = Io<T>::ld(F.ex + idx + dj);
+            const float hxo = Io<T>::ld(F.hx + idx), hyo = Io<T>::ld(F.hy + idx), hzo = Io<T>::ld(F.hz + idx);
+            const float bxo = ax ? ax[t] : 0.f, byo = ay ? ay[t] : 0.f, bzo = az ? az[t] : 0.f;
+            const Coef z1 = B->cw[2][1][k], z0 = B->cw[2][0][k];
+            float bn;
+            if (yin && zin) {   // H_x(i, j+1/2, k+1/2)
+                const float h = upml_h2(hxo, curl2(ezj, ezc, eyu, eyc, Sy, Sz), y1, z1, x0, ax != nullptr, bxo, bn);
+                Io<T>::st(F.ohx + idx, h);
+                if (ax) ax[t] = bn;
+            }
+            if (xin && zin) {   // H_y(i+1/2, j, k+1/2)
+                const float h = upml_h2(hyo, curl2(exu, exc, ezi, ezc, Sz, Sx), z1, x1, y0, ay != nullptr, byo, bn);
+                Io<T>::st(F.ohy + idx, h);
+                if (ay) ay[t] = bn;
+            }
+            if (xin && yin) {   // H_z(i+1/2, j+1/2, k)
+                const float h = upml_h2(hzo, curl2(eyi, eyc, exj, exc, Sx, Sy), x1, y1, z0, az != nullptr, bzo, bn);
+                Io<T>::st(F.ohz + idx, h);
+                if (az) az[t] = bn;
+            }
+            eyc = eyu;
+            exc = exu;
+            idx += P;
+            t += sc.nij;
         }
     }
 }
 
-// H~^{n+1/2} at `in` or, when `outside` the grid, its image across the wall:
-// PMC mirrors tangential H with a sign change, PEC gives 0.
-template <typename T>
-__device__ __forceinline__ float hwall(const T *h, bool outside, int wall, long long in, long long mirror)
-{
-    if (!outside) return Io<T>::ld(h + in);
-    return wall == 1 ? -Io<T>::ld(h + mirror) : 0.0f;
-}
+// Offset of H~ at a neighbour `in` or, when it lies `outside` the grid, of its
+// image `mirror` across the wall; wall_sign gives the image's factor (PMC:
+// odd mirror of tangential H, -1; PEC: 0).
+__device__ __forceinline__ long long hoff(bool outside, long long in, long long mirror) { return outside ? mirror : in; }
+__device__ __forceinline__ float hsign(bool outside, int wall) { return outside ? (wall == 1 ? -1.0f : 0.0f) : 1.0f; }
 
 template <typename T>
 __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
 {
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
-        SlabPos sp;
-        if (!slab_locate(plan, blk, B, sp)) continue;
+        SlabCol sc;
+        if (!slab_locate(plan, blk, B, sc)) continue;
         const long long step = *((volatile long long *)B->step);
         const Fields<T> F(B, (int)(step & 1));
-        const int i = sp.i, j = sp.j, k = sp.k;
+        const int i = sc.i, j = sc.j;
         const int nx = B->nx, ny = B->ny, nz = B->nz;
         const int X = B->pitch;
         const long long P = B->plane;
-        const long long idx = (long long)k * P + (long long)j * X + i;
         const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
-        const Slab &sl = *sp.sl;
-        const float4 ce = __ldg(B->ctab + cid_at(B, idx));
+        const Slab &sl = *sc.sl;
+        float *const ax = sl.aux[0], *const ay = sl.aux[1], *const az = sl.aux[2];
         const int *w = B->wall;
-        if (i < nx) {   // E_x(i+1/2, j, k)
-            const float hz1 = hwall(F.ohz, j == ny, w[3], idx, idx - X);
-            const float hz0 = hwall(F.ohz, j == 0, w[2], idx - X, idx);
-            const float hy1 = hwall(F.ohy, k == nz, w[5], idx, idx - P);
-            const float hy0 = hwall(F.ohy, k == 0, w[4], idx - P, idx);
-            const float sc = curl2(hz1, hz0, hy1, hy0, Sy, Sz);
-            const float e = upml_e(Io<T>::ld(F.ex + idx), sc, ce.x, B->cw[1][0][j], B->cw[2][0][k], B->cw[0][1][i],
-                                   sl.aux[0], sp.t);
-            Io<T>::st(F.oex + idx, e);
-        }
-        if (j < ny) {   // E_y(i, j+1/2, k)
-            const float hx1 = hwall(F.ohx, k == nz, w[5], idx, idx - P);
-            const float hx0 = hwall(F.ohx, k == 0, w[4], idx - P, idx);
-            const float hz1 = hwall(F.ohz, i == nx, w[1], idx, idx - 1);
-            const float hz0 = hwall(F.ohz, i == 0, w[0], idx - 1, idx);
-            const float sc = curl2(hx1, hx0, hz1, hz0, Sz, Sx);
-            const float e = upml_e(Io<T>::ld(F.ey + idx), sc, ce.y, B->cw[2][0][k], B->cw[0][0][i], B->cw[1][1][j],
-                                   sl.aux[1], sp.t);
-            Io<T>::st(F.oey + idx, e);
-        }
-        if (k < nz) {   // E_z(i, j, k+1/2)
-            const float hy1 = hwall(F.ohy, i == nx, w[1], idx, idx - 1);
-            const float hy0 = hwall(F.ohy, i == 0, w[0], idx - 1, idx);
-            const float hx1 = hwall(F.ohx, j == ny, w[3], idx, idx - X);
-            const float hx0 = hwall(F.ohx, j == 0, w[2], idx - X, idx);
-            const float sc = curl2(hy1, hy0, hx1, hx0, Sx, Sy);
-            const float e = upml_e(Io<T>::ld(F.ez + idx), sc, ce.z, B->cw[0][0][i], B->cw[1][0][j], B->cw[2][1][k],
-                                   sl.aux[2], sp.t);
-            Io<T>::st(F.oez + idx, e);
+        // images across the x and y walls (fixed along the column)
+        const bool xhi = i == nx, xlo = i == 0, yhi = j == ny, ylo = j == 0;
+        const float sxh = hsign(xhi, w[1]), sxl = hsign(xlo, w[0]), syh = hsign(yhi, w[3]), syl = hsign(ylo, w[2]);
+        const int ox1 = xhi ? -1 : 0, ox0 = xlo ? 0 : -1;   // offsets of H at i and i-1 (or images)
+        const int oy1 = yhi ? -X : 0, oy0 = ylo ? 0 : -X;
+        // factors fixed along the column: E_x (y integer, x half), E_y (x
+        // integer, y half), E_z (x integer, y integer)
+        const Coef y0 = B->cw[1][0][j], x1 = B->cw[0][1][i], x0 = B->cw[0][0][i], y1 = B->cw[1][1][j];
+        long long idx = (long long)sc.kbeg * P + (long long)j * X + i;
+        long long t = sc.t;
+#pragma unroll
+        for (int m = 0; m < kSlabKz; ++m) {
+            const int k = sc.kbeg + m;
+            if (k >= sc.kend) break;
+            const bool zhi = k == nz, zlo = k == 0;
+            const float szh = hsign(zhi, w[5]), szl = hsign(zlo, w[4]);
+            const long long oz1 = zhi ? -P : 0, oz0 = zlo ? 0 : -P;
+            const float4 ce = __ldg(B->ctab + cid_at(B, idx));
+            const Coef z0 = B->cw[2][0][k], z1 = B->cw[2][1][k];
+            // H~ at the node and its -x, -y, -z neighbours (or their images)
+            const float hz_y1 = syh * Io<T>::ld(F.ohz + idx + oy1), hz_y0 = syl * Io<T>::ld(F.ohz + idx + oy0);
+            const float hy_z1 = szh * Io<T>::ld(F.ohy + idx + oz1), hy_z0 = szl * Io<T>::ld(F.ohy + idx + oz0);
+            const float hx_z1 = szh * Io<T>::ld(F.ohx + idx + oz1), hx_z0 = szl * Io<T>::ld(F.ohx + idx + oz0);
+            const float hz_x1 = sxh * Io<T>::ld(F.ohz + idx + ox1), hz_x0 = sxl * Io<T>::ld(F.ohz + idx + ox0);
+            const float hy_x1 = sxh * Io<T>::ld(F.ohy + idx + ox1), hy_x0 = sxl * Io<T>::ld(F.ohy + idx + ox0);
+            const float hx_y1 = syh * Io<T>::ld(F.ohx + idx + oy1), hx_y0 = syl * Io<T>::ld(F.ohx + idx + oy0);
+            const float exo = Io<T>::ld(F.ex + idx), eyo = Io<T>::ld(F.ey + idx), ezo = Io<T>::ld(F.ez + idx);
+            const float dxo = ax ? ax[t] : 0.f, dyo = ay ? ay[t] : 0.f, dzo = az ? az[t] : 0.f;
+            float dn;
+            if (i < nx) {   // E_x(i+1/2, j, k)
+                const float e = upml_e2(exo, curl2(hz_y1, hz_y0, hy_z1, hy_z0, Sy, Sz), ce.x, y0, z0, x1,
+                                        ax != nullptr, dxo, dn);
+                Io<T>::st(F.oex + idx, e);
+                if (ax) ax[t] = dn;
+            }
+            if (j < ny) {   // E_y(i, j+1/2, k)
+                const float e = upml_e2(eyo, curl2(hx_z1, hx_z0, hz_x1, hz_x0, Sz, Sx), ce.y, z0, x0, y1,
+                                        ay != nullptr, dyo, dn);
+                Io<T>::st(F.oey + idx, e);
+                if (ay) ay[t] = dn;
+            }
+            if (k < nz) {   // E_z(i, j, k+1/2)
+                const float e = upml_e2(ezo, curl2(hy_x1, hy_x0, hx_y1, hx_y0, Sx, Sy), ce.z, x0, y0, z1,
+                                        az != nullptr, dzo, dn);
+                Io<T>::st(F.oez + idx, e);
+                if (az) az[t] = dn;
+            }
+            idx += P;
+            t += sc.nij;
         }
     }
 }
