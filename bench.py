@@ -12,11 +12,12 @@ value  = cell-updates / s (Gcell-updates/s) with inputs resident in HBM.
 e2e    = the same metric through the C-ABI with host buffers: every step
          re-uploads the material volume (fdtd_set_materials, host -> device),
          runs the window and copies the spectra back (device -> host).
-roofline: the fused interior kernel (the dominant one), algorithmic bytes per
-         interior node-update (49 B in FP32: 6 fields read + written, 1 id
+roofline: the fused interior launch (the dominant kernel), algorithmic
+         bytes per node-update (49 B in FP32: 6 fields read + written, 1 id
          byte; 25 B with 16-bit storage) over its mean launch time measured
          with CUDA events on its stream, against the measured HBM copy
-         bandwidth.
+         bandwidth; the z-UPML launch (+32 B of auxiliaries per node) is
+         reported beside it.
 cpu_baseline: the FP64 oracle on the same full-size grid for a few steps.
 
 Other workloads: --workload small | realistic | batched | served.
@@ -113,6 +114,19 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(x: float) -> float:
+    """Max of a per-rank float over all ranks (identity on one rank): the
+    bench's whole-job time.  NCCL reduces a device tensor, gloo a host one."""
+    import torch
+    dist = torch.distributed
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _workload(name: str, seed_offset: int = 0):
     from paper_1008_2602_gb300 import workloads as W
     if name == "small":
@@ -187,10 +201,7 @@ def run_single(args, world, rank, local):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
     elapsed = t1 - t0
-    if world > 1:
-        t = torch.tensor([elapsed], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = _max_over_ranks(elapsed)
     dev_ms = float(phase.sum())
     total_updates = float(cells) * window * args.steps * world
     value = total_updates / elapsed / 1e9
@@ -227,10 +238,7 @@ def run_single(args, world, rank, local):
             s.spectra_into(spec)            # D2H of the FP64 spectra (synchronises)
         te1 = time.perf_counter()
         et = te1 - te0
-        if world > 1:
-            t = torch.tensor([et], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            et = float(t.item())
+        et = _max_over_ranks(et)
         pitch = ((prob.nx + 1 + 63) // 64) * 64
         h2d = pitch * (prob.ny + 1) * (prob.nz + 1) + 256 * 16
         e2e = {"value": float(cells) * window * args.e2e_steps * world / et / 1e9, "unit": "Gcell-updates/s",
@@ -342,10 +350,7 @@ def run_batched(args, world, rank, local):
                 last[0].close()
             last = (b, sols)
     el = sum(times)
-    if world > 1:
-        t = torch.tensor([el], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        el = float(t.item())
+    el = _max_over_ranks(el)
     value = len(probs) * args.steps * world / el
     # per-board plain launches on the same GPU, and identity of the results
     plain_t, plain_tr = _plain_solves(probs[: args.plain_boards], args.precision)

@@ -93,7 +93,7 @@ struct fdtd_ctx {
     long long host_step = 0;
     fdtd_batch *batch = nullptr;
     // single-board plan and graph
-    fdtd_tuning tune{62, 4, 25, 16};
+    fdtd_tuning tune{62, 4, 10, 16};
     bool plan_dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;   // device [0]=board ptr, then prefixes
@@ -114,7 +114,7 @@ struct fdtd_batch {
     bool own_stream = false;
     std::vector<fdtd_ctx *> members;
     std::vector<long long> remaining;
-    fdtd_tuning tune{62, 4, 25, 16};
+    fdtd_tuning tune{62, 4, 10, 16};
     bool dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;

@@ -15,7 +15,7 @@ import time
 from typing import Dict, Iterable, List, Optional, Sequence
 
 SHAPES = [(62, 4), (124, 4), (62, 8), (124, 8)]
-ZSEGS = [16, 25, 50]
+ZSEGS = [8, 10, 16, 25]
 CHUNKS = [16, 64]
 
 CACHE = os.environ.get("FDTD_TUNE_CACHE",
