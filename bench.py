@@ -219,6 +219,10 @@ def run_single(args, world, rank, local):
     t_zp = phase[1] / 1e3 / n_launch
     achieved = alg_bytes / t_int / 1e9
     zp_bytes = (bytes_per_node + 32) * upml_nodes
+    # whole leapfrog step: every node's 12 field values + id, the z-UPML
+    # auxiliaries and the slab auxiliaries (each read and written once)
+    step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 32 * upml_nodes + 8 * inf["slab_aux_values"]
+    t_leap = elapsed / (window * args.steps)
     peak, peak_kind = _measured_peaks()
     traffic = _traffic_for(f"k_fused_interior_{args.precision}", int_nodes)
 
@@ -263,6 +267,12 @@ def run_single(args, world, rank, local):
                      "traffic": traffic, "peak_source": peak_kind,
                      "bytes_per_unit": bytes_per_node, "units_per_launch": int_nodes,
                      "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": round(t_int * 1e3, 5)},
+        "roofline_step": {"what": "whole leapfrog step (all kernels, wall time per step)",
+                          "algorithmic_bytes_per_step": int(step_bytes),
+                          "bytes_per_cell": round(step_bytes / cells, 2),
+                          "achieved": round(step_bytes / t_leap / 1e9, 1), "peak": peak, "unit": "GB/s",
+                          "frac": round(step_bytes / t_leap / 1e9 / peak, 4),
+                          "roofline_gcell_updates_per_s": round(cells / (step_bytes / (peak * 1e9)) / 1e9, 2)},
         "roofline_zupml": {"kernel": "k_fused z-UPML launch", "bytes_per_unit": bytes_per_node + 32,
                            "units_per_launch": upml_nodes, "mean_launch_ms": round(t_zp * 1e3, 5),
                            "achieved": round(zp_bytes / t_zp / 1e9, 1) if t_zp > 0 else None,

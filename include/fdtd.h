@@ -98,6 +98,7 @@ typedef struct {
     long long slab_nodes;      /* nodes updated by the UPML/boundary slab kernels */
     long long device_bytes;    /* device memory held */
     int n_combo;               /* distinct per-node E-coefficient triples */
+    long long slab_aux_values; /* auxiliary D~/B~ values held by the slabs (read and written once per step) */
 } fdtd_info_t;
 
 /* Create a board (Model section, Fig. 1).

@@ -1134,9 +1134,14 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
     info->interior_nodes = (Lx > 0 && Ly > 0 && Lz > 0) ? Lx * Ly * Lz : 0;
     info->fused_upml_nodes = info->interior_nodes > 0 ? Lx * Ly * (c->zplanes[0] + c->zplanes[1]) : 0;
-    long long sn = 0;
-    for (int s = 0; s < h.n_slab; ++s) sn += h.slab[s].n;
+    long long sn = 0, sa = 0;
+    for (int s = 0; s < h.n_slab; ++s) {
+        sn += h.slab[s].n;
+        for (int a = 0; a < 6; ++a)
+            if (h.slab[s].aux[a]) sa += h.slab[s].n;
+    }
     info->slab_nodes = sn;
+    info->slab_aux_values = sa;
     info->device_bytes = c->device_bytes;
     info->n_combo = c->n_combo;
     return FDTD_OK;
