@@ -16,7 +16,7 @@ roofline: the fused interior launch (the dominant kernel), algorithmic
          bytes per node-update (49 B in FP32: 6 fields read + written, 1 id
          byte; 25 B with 16-bit storage) over its mean launch time measured
          with CUDA events on its stream, against the measured HBM copy
-         bandwidth; the z-UPML launch (+32 B of auxiliaries per node) is
+         bandwidth; the z-UPML launch (+16 B of auxiliaries per node) is
          reported beside it.
 cpu_baseline: the FP64 oracle on the same full-size grid for a few steps.
 
@@ -207,8 +207,8 @@ def run_single(args, world, rank, local):
     value = total_updates / elapsed / 1e9
 
     # roofline of the dominant kernel, the fused interior launch: 12 field
-    # values + 1 id byte per node.  The z-UPML launch also moves 4 FP32
-    # auxiliaries read and 4 written per node (reported beside it).
+    # values + 1 id byte per node.  The z-UPML launch also reads and writes
+    # the B~z and D~z auxiliaries of each node (reported beside it).
     es = 4 if args.precision == "fp32" else 2
     bytes_per_node = 12 * es + (2 if inf["n_combo"] > 256 else 1)
     upml_nodes = inf["fused_upml_nodes"]
@@ -218,10 +218,10 @@ def run_single(args, world, rank, local):
     t_int = phase[2] / 1e3 / n_launch
     t_zp = phase[1] / 1e3 / n_launch
     achieved = alg_bytes / t_int / 1e9
-    zp_bytes = (bytes_per_node + 32) * upml_nodes
+    zp_bytes = (bytes_per_node + 16) * upml_nodes
     # whole leapfrog step: every node's 12 field values + id, the z-UPML
     # auxiliaries and the slab auxiliaries (each read and written once)
-    step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 32 * upml_nodes + 8 * inf["slab_aux_values"]
+    step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 16 * upml_nodes + 8 * inf["slab_aux_values"]
     t_leap = elapsed / (window * args.steps)
     peak, peak_kind = _measured_peaks()
     traffic = _traffic_for(f"k_fused_interior_{args.precision}", int_nodes)
@@ -273,7 +273,7 @@ def run_single(args, world, rank, local):
                           "achieved": round(step_bytes / t_leap / 1e9, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(step_bytes / t_leap / 1e9 / peak, 4),
                           "roofline_gcell_updates_per_s": round(cells / (step_bytes / (peak * 1e9)) / 1e9, 2)},
-        "roofline_zupml": {"kernel": "k_fused z-UPML launch", "bytes_per_unit": bytes_per_node + 32,
+        "roofline_zupml": {"kernel": "k_fused z-UPML launch", "bytes_per_unit": bytes_per_node + 16,
                            "units_per_launch": upml_nodes, "mean_launch_ms": round(t_zp * 1e3, 5),
                            "achieved": round(zp_bytes / t_zp / 1e9, 1) if t_zp > 0 else None,
                            "frac": round(zp_bytes / t_zp / 1e9 / peak, 4) if t_zp > 0 else None},

@@ -94,7 +94,7 @@ typedef struct {
     int n_bins;                /* DFT bins q = 0..n_bins-1, f_q = q / (N dt) */
     int precision;
     long long interior_nodes;  /* nodes updated by the fused interior kernel */
-    long long fused_upml_nodes;/* of those, nodes in z-UPML planes (carry D~y, D~z, B~y, B~z) */
+    long long fused_upml_nodes;/* of those, nodes in z-UPML planes (carry D~z and B~z) */
     long long slab_nodes;      /* nodes updated by the UPML/boundary slab kernels */
     long long device_bytes;    /* device memory held */
     int n_combo;               /* distinct per-node E-coefficient triples */

@@ -458,15 +458,13 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
     const uint64_t Ly = h.iy1 - h.iy0;
     for (int bx = 0; bx < 2; ++bx) {
         if (!c->zplanes[bx]) continue;
-        for (int a = 0; a < 2; ++a) {
-            if (int r = encode3d(&maps[tm_zd(bx, a)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zD[bx][a], h.zpitch, Ly,
-                                 c->zplanes[bx], box_a(tx), ty))
+        if (int r = encode3d(&maps[tm_zd(bx)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zD[bx], h.zpitch, Ly,
+                             c->zplanes[bx], box_a(tx), ty))
+            return r;
+        for (int par = 0; par < 2; ++par)
+            if (int r = encode3d(&maps[tm_zb(bx, par)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zB[bx][par], h.zpitch,
+                                 Ly, c->zplanes[bx], box_a(tx), ty + 1))
                 return r;
-            for (int par = 0; par < 2; ++par)
-                if (int r = encode3d(&maps[tm_zb(bx, a, par)], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, h.zB[bx][a][par],
-                                     h.zpitch, Ly, c->zplanes[bx], box_a(tx), ty + 1))
-                    return r;
-        }
     }
     // a fresh buffer per encoding: a descriptor address is never rewritten
     // while a kernel may still hold it in its descriptor cache
@@ -802,12 +800,15 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
             return false;
         };
         for (int comp = 0; comp < 6; ++comp) {
-            const int w = comp % 3, w1 = (w + 1) % 3;
+            const int w = comp % 3, w1 = (w + 1) % 3, w2 = (w + 2) % 3;
             const bool is_h = comp >= 3;
-            // E: D recurrence along w1 (integer), D->E along w (half)
-            // H: B recurrence along w1 (half),    B->H along w (integer)
-            const bool need = any_nontrivial(w1, is_h ? 1 : 0, true, false) ||
-                              any_nontrivial(w, is_h ? 0 : 1, false, true);
+            // E: D recurrence along w1, E recurrence along w2 (integer), D->E along w (half)
+            // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
+            // An auxiliary is needed where D->E (B->H) is graded or both
+            // recurrences are; otherwise the lossy form holds exactly.
+            const int rec = is_h ? 1 : 0;
+            const bool need = any_nontrivial(w, is_h ? 0 : 1, false, true) ||
+                              (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
             sl.aux[comp] = nullptr;
             if (need && !r) {
                 r = dalloc(c, &sl.aux[comp], sizeof(float) * (size_t)sl.n);
@@ -817,26 +818,22 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     }
     // z-UPML auxiliaries of the fused region: lower box planes [1, iz0), upper [iz1, nz)
     for (int bx = 0; bx < 2; ++bx) {
-        for (int a = 0; a < 2; ++a) {
-            h.zD[bx][a] = nullptr;
-            h.zB[bx][a][0] = h.zB[bx][a][1] = nullptr;
-        }
+        h.zD[bx] = nullptr;
+        h.zB[bx][0] = h.zB[bx][1] = nullptr;
         if (!fused) continue;
         const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
         if (planes <= 0) continue;
         h.zpitch = ((h.ix1 - h.ix0) + 7) & ~7;
         const size_t n = (size_t)planes * h.zpitch * (h.iy1 - h.iy0);
         c->zplanes[bx] = planes;
-        for (int a = 0; a < 2 && !r; ++a) {
-            float *ptr[3] = {nullptr, nullptr, nullptr};
-            for (int t = 0; t < 3 && !r; ++t) {
-                r = dalloc(c, &ptr[t], sizeof(float) * n);
-                if (!r) { cudaError_t e = cudaMemsetAsync(ptr[t], 0, sizeof(float) * n, c->cur); if (e) r = cuda_fail(e, "memset"); }
-            }
-            h.zD[bx][a] = ptr[0];
-            h.zB[bx][a][0] = ptr[1];
-            h.zB[bx][a][1] = ptr[2];
+        float *ptr[3] = {nullptr, nullptr, nullptr};   // D~z, B~z (two parities)
+        for (int t = 0; t < 3 && !r; ++t) {
+            r = dalloc(c, &ptr[t], sizeof(float) * n);
+            if (!r) { cudaError_t e = cudaMemsetAsync(ptr[t], 0, sizeof(float) * n, c->cur); if (e) r = cuda_fail(e, "memset"); }
         }
+        h.zD[bx] = ptr[0];
+        h.zB[bx][0] = ptr[1];
+        h.zB[bx][1] = ptr[2];
         c->zaux_n[bx] = n;
     }
     h.slab_blocks = blocks;
@@ -1079,12 +1076,11 @@ int fdtd_reset(fdtd_ctx *c)
     for (int s = 0; s < h.n_slab; ++s)
         for (int a = 0; a < 6; ++a)
             if (h.slab[s].aux[a]) CK(cudaMemsetAsync(h.slab[s].aux[a], 0, sizeof(float) * (size_t)h.slab[s].n, c->cur));
-    for (int bx = 0; bx < 2; ++bx)
-        for (int a = 0; a < 2; ++a) {
-            if (h.zD[bx][a]) CK(cudaMemsetAsync(h.zD[bx][a], 0, sizeof(float) * c->zaux_n[bx], c->cur));
-            for (int p = 0; p < 2; ++p)
-                if (h.zB[bx][a][p]) CK(cudaMemsetAsync(h.zB[bx][a][p], 0, sizeof(float) * c->zaux_n[bx], c->cur));
-        }
+    for (int bx = 0; bx < 2; ++bx) {
+        if (h.zD[bx]) CK(cudaMemsetAsync(h.zD[bx], 0, sizeof(float) * c->zaux_n[bx], c->cur));
+        for (int p = 0; p < 2; ++p)
+            if (h.zB[bx][p]) CK(cudaMemsetAsync(h.zB[bx][p], 0, sizeof(float) * c->zaux_n[bx], c->cur));
+    }
     if (h.trace) CK(cudaMemsetAsync(h.trace, 0, sizeof(float) * (size_t)h.n_probe * h.n_total, c->cur));
     if (h.dft) CK(cudaMemsetAsync(h.dft, 0, sizeof(double) * 2 * (size_t)h.n_probe * std::max(h.n_bins, 1), c->cur));
     CK(cudaMemsetAsync(h.step, 0, sizeof(long long), c->cur));

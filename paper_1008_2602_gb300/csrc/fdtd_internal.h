@@ -20,6 +20,16 @@
 // (ce_x, ce_y, ce_z) = 1/eps_r of its three E edges (0 on PEC) of a table.
 // UPML factors are 1D per axis at integer and half positions.
 //
+// Which auxiliaries are stored.  With H~' = b1_{w+2} H~ + g_{w+2} (ap_w B~' -
+// am_w B~) and B~' = b1_{w+1} B~ - g_{w+1} S curl: if the factors along w are
+// trivial (ap = am = 1) and at most one of w+1, w+2 is graded, B~' - B~ is a
+// known multiple of the curl or H~ - B~ is constant in time (zero, since both
+// start at zero), so the component updates as the lossy Yee form
+// H~' = (b1_{w+1} b1_{w+2}) H~ - (g_{w+1} g_{w+2}) S curl with no auxiliary
+// (one of each product is exactly 1).  Likewise E' = (b1 b1) E + ce (g g) S curl
+// (E - ce D~ is constant).  An auxiliary is kept only where the factors along
+// w are graded or both w+1 and w+2 are.
+//
 // Work split.  The fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) (the
 // columns outside the x/y UPML, minus the two outer z planes) is updated by
 // one fused H+E kernel that marches z; its z-UPML planes ([1,iz0) and
@@ -92,9 +102,11 @@ struct Board {
     int depth[6];                 // UPML cells per face
     int ix0, ix1, iy0, iy1, iz0, iz1;   // fused xy box; non-UPML z range [iz0, iz1)
     // z-UPML boxes of the fused region: [0] k in [1, iz0), [1] k in [iz1, nz);
-    // element (i, j, k) at ((k - k0) * (iy1 - iy0) + j - iy0) * zpitch + i - ix0
-    float *zD[2][2];              // [box][y, z]         D~y, D~z
-    float *zB[2][2][2];           // [box][y, z][parity] B~y, B~z
+    // element (i, j, k) at ((k - k0) * (iy1 - iy0) + j - iy0) * zpitch + i - ix0.
+    // With sigma_z alone, B~x, B~y and D~x, D~y need no storage (see the
+    // auxiliary rule below); B~z and D~z are kept.
+    float *zD[2];                 // [box]         D~z
+    float *zB[2][2];              // [box][parity] B~z
     int zpitch;                   // row pitch of the z-UPML boxes (multiple of 8)
     int tm_tx, tm_ty;             // tile shape the tensor maps were encoded for
     const CUtensorMap *tm;        // kNumMaps TMA descriptors (see tm_* below)
@@ -134,9 +146,9 @@ struct Plan {
 __host__ __device__ constexpr int tm_e(int par, int c) { return par * 3 + c; }               // E   box_e  x (TY+2)
 __host__ __device__ constexpr int tm_h(int par, int c) { return 6 + par * 3 + c; }           // H   box_h  x (TY+1)
 constexpr int kTmCid = 12;                                                // ids box_c* x TY
-__host__ __device__ constexpr int tm_zd(int box, int a) { return 13 + box * 2 + a; }         // D~  box_a  x TY
-__host__ __device__ constexpr int tm_zb(int box, int a, int par) { return 17 + (box * 2 + a) * 2 + par; }   // B~ box_a x (TY+1)
-constexpr int kNumMaps = 25;
+__host__ __device__ constexpr int tm_zd(int box) { return 13 + box; }                         // D~z box_a  x TY
+__host__ __device__ constexpr int tm_zb(int box, int par) { return 15 + box * 2 + par; }        // B~z box_a  x (TY+1)
+constexpr int kNumMaps = 19;
 // TMA box widths for a tile of tx columns (x rounded down to 16 bytes)
 __host__ __device__ constexpr int box_up(int x, int m) { return (x + m - 1) / m * m; }
 __host__ __device__ constexpr int box_e(int tx) { return box_up(tx + 9, 8); }

@@ -101,7 +101,9 @@ __device__ __forceinline__ float upml_h2(float h, float scurl, const Coef &a, co
         Bn = __fmaf_rn(-a.g, scurl, __fmul_rn(a.b1, Bo));
         return __fmaf_rn(bb.g, __fmaf_rn(c.ap, Bn, -__fmul_rn(c.am, Bo)), __fmul_rn(bb.b1, h));
     }
-    return __fmaf_rn(-bb.g, scurl, __fmul_rn(bb.b1, h));
+    // no auxiliary: c is trivial and at most one of a, bb is graded, so the
+    // products below are exact
+    return __fmaf_rn(-__fmul_rn(a.g, bb.g), scurl, __fmul_rn(__fmul_rn(a.b1, bb.b1), h));
 }
 
 // Same for E (D~ along w+1, E along w+2, D~->E along w); ce = 1/eps_r.
@@ -112,7 +114,8 @@ __device__ __forceinline__ float upml_e2(float e, float scurl, float ce, const C
         Dn = __fmaf_rn(a.g, scurl, __fmul_rn(a.b1, Do));
         return __fmaf_rn(__fmul_rn(ce, bb.g), __fmaf_rn(c.ap, Dn, -__fmul_rn(c.am, Do)), __fmul_rn(bb.b1, e));
     }
-    return __fmaf_rn(__fmul_rn(ce, bb.g), scurl, __fmul_rn(bb.b1, e));
+    // no auxiliary (see upml_h2)
+    return __fmaf_rn(__fmul_rn(ce, __fmul_rn(a.g, bb.g)), scurl, __fmul_rn(__fmul_rn(a.b1, bb.b1), e));
 }
 
 __device__ __constant__ Coef kOne = {1.0f, 1.0f, 1.0f, 1.0f};
@@ -127,8 +130,8 @@ __device__ __forceinline__ long long zaux_index(const Board *B, int box, int i, 
 }
 
 // New H~x, H~y, H~z at a fused-region node from already-fetched operands.
-// In z-UPML planes only sigma_z is non-zero: H~x has no auxiliary, H~y and
-// H~z carry B~y, B~z.
+// In z-UPML planes only sigma_z is non-zero: H~x and H~y update in the lossy
+// form (no auxiliary), H~z carries B~z.
 struct ZCoef {
     Coef zi, zh;   // z factors at the node's integer and half positions
 };
@@ -139,10 +142,11 @@ __device__ __forceinline__ float fused_hx(float h, float sc, int zb, const ZCoef
     if (!zb) return __fsub_rn(h, sc);
     return upml_h2(h, sc, kOne, z.zh, kOne, false, 0.f, dummy);
 }
-__device__ __forceinline__ float fused_hy(float h, float sc, int zb, const ZCoef &z, float Bo, float &Bn)
+__device__ __forceinline__ float fused_hy(float h, float sc, int zb, const ZCoef &z)
 {
+    float dummy;
     if (!zb) return __fsub_rn(h, sc);
-    return upml_h2(h, sc, z.zh, kOne, kOne, true, Bo, Bn);
+    return upml_h2(h, sc, z.zh, kOne, kOne, false, 0.f, dummy);
 }
 __device__ __forceinline__ float fused_hz(float h, float sc, int zb, const ZCoef &z, float Bo, float &Bn)
 {
@@ -293,7 +297,7 @@ constexpr int kWarpCols = 62;
 //   E  3 x (TY+2) x EW   rows j0-1 .. j0+TY
 //   H  3 x (TY+1) x HW   rows j0-1 .. j0+TY-1
 //   id TY x C8W bytes (or TY x C16W uint16), rows j0 .. j0+TY-1
-//   z-UPML kernel only: B~y, B~z (TY+1) x AW and D~y, D~z TY x AW floats
+//   z-UPML kernel only: B~z (TY+1) x AW and D~z TY x AW floats
 // Every box starts 128-byte aligned.
 template <typename T, int TY, int W, bool ZP>
 struct Stage {
@@ -308,13 +312,13 @@ struct Stage {
     static constexpr int C8_BYTES = TY * C8W, C16_BYTES = TY * C16W * 2;
     static constexpr int B_COMP = (TY + 1) * AW, D_COMP = TY * AW;
     static constexpr int B_CS = al(B_COMP * 4) / 4, D_CS = al(D_COMP * 4) / 4;
-    static constexpr int A_BYTES = 2 * (B_COMP + D_COMP) * 4;
+    static constexpr int A_BYTES = (B_COMP + D_COMP) * 4;
     static constexpr int E_OFF = 0;
     static constexpr int H_OFF = 3 * E_CS * ES;
     static constexpr int C_OFF = H_OFF + 3 * H_CS * ES;
     static constexpr int ITEM_OFF = (C_OFF + (C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES) + 7) & ~7;   // item id
     static constexpr int A_OFF = al(ITEM_OFF + 8);
-    static constexpr int BYTES = A_OFF + (ZP ? 2 * (B_CS + D_CS) * 4 : 0);
+    static constexpr int BYTES = A_OFF + (ZP ? (B_CS + D_CS) * 4 : 0);
 };
 
 template <typename T, int TY, int W, int NS, bool ZP>
@@ -390,7 +394,7 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 // Warps 0..W-1 compute; warp W (one lane) is the producer, streaming planes
 // kstart..ke of the tile into an NS-stage ring (E^n with a one-node halo,
 // H~^{n-1/2} with the low halo row and column, coefficient ids, and in the
-// z-UPML kernel the B~/D~ auxiliaries of z-UPML planes), each stage with a
+// z-UPML kernel the B~z/D~z auxiliaries of z-UPML planes), each stage with a
 // "full" mbarrier (TMA bytes) and an "empty" one (one arrival per compute
 // warp).  Compute warp w owns 62 columns [i0 + 62w, i0 + 62w + 62); lane l
 // holds the column pair (g + 2l, g + 2l + 1), g = (i0 + 62w - 1) & ~1, so
@@ -402,9 +406,9 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 // of halo nodes outside the fused region is read from the slab kernel's
 // output instead.  The plane below the segment is run once for the tile's
 // H~x, H~y there (or read, see decode_tile); the plane above is read for E
-// only.  In z-UPML planes (sigma_z only) H~y, H~z carry B~y, B~z and E_y,
-// E_z carry D~y, D~z; those planes use the scalar update helpers per
-// element, every other plane the paired form, with identical rounding.
+// only.  In z-UPML planes (sigma_z only) H~z carries B~z and E_z carries
+// D~z, while H~x, H~y, E_x, E_y update in the lossy form; those planes use
+// the scalar update helpers per element, every other plane the paired form.
 template <typename T, int TY, int W, int NS, bool ZP>
 __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::MINB)) k_fused(Plan plan)
 {
@@ -477,11 +481,8 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                 if (zb) {
                     const int bx = zb - 1, kz = p - (zb == 1 ? 1 : B->iz1);
                     unsigned char *a = st + St::A_OFF;
-                    tma_load_3d(a, tm + tm_zb(bx, 0, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
-                    tma_load_3d(a + St::B_CS * 4, tm + tm_zb(bx, 1, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
-                    tma_load_3d(a + 2 * St::B_CS * 4, tm + tm_zd(bx, 0), xa0, t.j0 - B->iy0, kz, &full[s]);
-                    tma_load_3d(a + 2 * St::B_CS * 4 + St::D_CS * 4, tm + tm_zd(bx, 1), xa0, t.j0 - B->iy0, kz,
-                                &full[s]);
+                    tma_load_3d(a, tm + tm_zb(bx, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
+                    tma_load_3d(a + St::B_CS * 4, tm + tm_zd(bx), xa0, t.j0 - B->iy0, kz, &full[s]);
                 }
             }
         }
@@ -559,17 +560,17 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
             const unsigned char *C0 = st0 + St::C_OFF;
             const float *A0 = reinterpret_cast<const float *>(st0 + St::A_OFF) + acol;
             constexpr int EW = St::EW, HW = St::HW, ECS = St::E_CS, HCS = St::H_CS;
-            constexpr int AW = St::AW, BCS = St::B_CS, DCS = St::D_CS;
+            constexpr int AW = St::AW, BCS = St::B_CS;
             const int zb = ZP ? (k < iz0 ? 1 : (k >= iz1 ? 2 : 0)) : 0;
             ZCoef z;
-            float *zdy = nullptr, *zdz = nullptr, *nzby = nullptr, *nzbz = nullptr;
+            float *zdz = nullptr, *nzbz = nullptr;
             long long za = 0;
             if (ZP && zb) {
                 z.zi = B->cw[2][0][k];
                 z.zh = B->cw[2][1][k];
                 za = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
-                nzby = B->zB[zb - 1][0][par ^ 1]; nzbz = B->zB[zb - 1][1][par ^ 1];
-                zdy = B->zD[zb - 1][0]; zdz = B->zD[zb - 1][1];
+                nzbz = B->zB[zb - 1][par ^ 1];
+                zdz = B->zD[zb - 1];
             }
             const bool full_plane = k >= kb;
             // coefficient rows of the lane's two nodes (ids clamped into the box,
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
             }
             // E^n at box row rr (own node), and H~^{n+1/2}(k) there from the staged planes
             auto hrow = [&](int rr, bool in_f, float2 &ex, float2 &ey, float2 &ez, float2 &hx, float2 &hy, float2 &hz,
-                            float2 &nby, float2 &nbz) {
+                            float2 &nbz) {
                 ez = Pair<T>::lds(E0 + 2 * ECS + rr * EW);
                 ey = Pair<T>::lds(E0 + ECS + rr * EW);
                 ex = Pair<T>::lds(E0 + rr * EW);
@@ -605,14 +606,13 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                     hy = sub2(ohy, scy);
                     hz = sub2(ohz, scz);
                 } else {
-                    // B~ of the node: box row rr; zero outside the fused rows
-                    float2 boy = make_float2(A0[rr * AW], A0[rr * AW + 1]);
-                    float2 boz = make_float2(A0[BCS + rr * AW], A0[BCS + rr * AW + 1]);
-                    if (!in_f) boy = boz = make_float2(0.f, 0.f);
+                    // B~z of the node: box row rr; zero outside the fused rows
+                    float2 boz = make_float2(A0[rr * AW], A0[rr * AW + 1]);
+                    if (!in_f) boz = make_float2(0.f, 0.f);
                     hx.x = fused_hx(ohx.x, scx.x, zb, z);
                     hx.y = fused_hx(ohx.y, scx.y, zb, z);
-                    hy.x = fused_hy(ohy.x, scy.x, zb, z, boy.x, nby.x);
-                    hy.y = fused_hy(ohy.y, scy.y, zb, z, boy.y, nby.y);
+                    hy.x = fused_hy(ohy.x, scy.x, zb, z);
+                    hy.y = fused_hy(ohy.y, scy.y, zb, z);
                     hz.x = fused_hz(ohz.x, scz.x, zb, z, boz.x, nbz.x);
                     hz.y = fused_hz(ohz.y, scz.y, zb, z, boz.y, nbz.y);
                 }
@@ -641,16 +641,16 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                         pz.y = Io<T>::ld(gp + 5 * NN + 1);
                     }
                 } else {
-                    float2 ex, ey, ez, hy, d0, d1;
-                    hrow(0, true, ex, ey, ez, px, hy, pz, d0, d1);
+                    float2 ex, ey, ez, hy, d0;
+                    hrow(0, true, ex, ey, ez, px, hy, pz, d0);
                     slab_fix(0, px, hy, pz);
                 }
             }
 #pragma unroll
             for (int r = 0; r < TY; ++r) {
                 const int j = j0 + r, rr = r + 1;
-                float2 ex, ey, ez, hx, hy, hz, nby = make_float2(0.f, 0.f), nbz = nby;
-                hrow(rr, j < iy1, ex, ey, ez, hx, hy, hz, nby, nbz);
+                float2 ex, ey, ez, hx, hy, hz, nbz = make_float2(0.f, 0.f);
+                hrow(rr, j < iy1, ex, ey, ez, hx, hy, hz, nbz);
                 slab_fix(rr, hx, hy, hz);
                 const float hyl = __shfl_up_sync(0xffffffffu, hy.y, 1);   // H~ at (ca-1, j)
                 const float hzl = __shfl_up_sync(0xffffffffu, hz.y, 1);
@@ -667,19 +667,17 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                         ezv = make_float2(__fmaf_rn(cea[r].z, scz.x, ez.x), __fmaf_rn(ceb[r].z, scz.y, ez.y));
                     } else {
                         const long long a = za + (long long)r * zrow;
-                        const float *dyo = A0 + 2 * BCS + r * AW, *dzo = dyo + DCS;
+                        const float *dzo = A0 + BCS + r * AW;   // D~z of the node (box row r)
                         float nd;
-                        float2 ndy, ndz;
+                        float2 ndz;
                         exv.x = upml_e2(ex.x, scx.x, cea[r].x, kOne, z.zi, kOne, false, 0.f, nd);
                         exv.y = upml_e2(ex.y, scx.y, ceb[r].x, kOne, z.zi, kOne, false, 0.f, nd);
-                        eyv.x = upml_e2(ey.x, scy.x, cea[r].y, z.zi, kOne, kOne, true, dyo[0], ndy.x);
-                        eyv.y = upml_e2(ey.y, scy.y, ceb[r].y, z.zi, kOne, kOne, true, dyo[1], ndy.y);
+                        eyv.x = upml_e2(ey.x, scy.x, cea[r].y, z.zi, kOne, kOne, false, 0.f, nd);
+                        eyv.y = upml_e2(ey.y, scy.y, ceb[r].y, z.zi, kOne, kOne, false, 0.f, nd);
                         ezv.x = upml_e2(ez.x, scz.x, cea[r].z, kOne, kOne, z.zh, true, dzo[0], ndz.x);
                         ezv.y = upml_e2(ez.y, scz.y, ceb[r].z, kOne, kOne, z.zh, true, dzo[1], ndz.y);
-                        if (own_a) { stg1(zdy + a, ndy.x); stg1(zdz + a, ndz.x); stg1(nzby + a, nby.x); stg1(nzbz + a, nbz.x); }
-                        if (own_b) {
-                            stg1(zdy + a + 1, ndy.y); stg1(zdz + a + 1, ndz.y); stg1(nzby + a + 1, nby.y); stg1(nzbz + a + 1, nbz.y);
-                        }
+                        if (own_a) { stg1(zdz + a, ndz.x); stg1(nzbz + a, nbz.x); }
+                        if (own_b) { stg1(zdz + a + 1, ndz.y); stg1(nzbz + a + 1, nbz.y); }
                     }
                     if (own_a && own_b) {
                         stg2(o + 3 * NN, hx); stg2(o + 4 * NN, hy); stg2(o + 5 * NN, hz);
