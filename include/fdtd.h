@@ -181,6 +181,31 @@ int fdtd_diagnostics(fdtd_ctx *ctx, double *energy, double *max_div_b);
  * counter (sources, probes and geometry stay).  Asynchronous. */
 int fdtd_reset(fdtd_ctx *ctx);
 
+/* Checkpoint.  fdtd_save copies the whole solver state to host memory: both
+ * field parities, every UPML auxiliary, the probe traces, the running-DFT
+ * accumulators and the step counters (the Model section's leapfrog state at
+ * step n), after a small header that identifies the board.  With buf == NULL
+ * or cap < the size, nothing is copied and *size receives the bytes needed
+ * (FDTD_OK).  The caller owns buf.  Synchronises.  Not for a context that is
+ * in a batch (FDTD_ESTATE).
+ * fdtd_load restores such a checkpoint into a context created from the same
+ * problem (grid, boundary, precision, materials, sources, probes, spectrum);
+ * a header that does not match returns FDTD_EINVAL and leaves the context
+ * unchanged.  Stepping a restored context continues bitwise as the saved
+ * one would have (fields and traces; the FP64 spectra agree to rounding,
+ * since the running DFT folds samples at chunk boundaries).  Synchronises. */
+int fdtd_save(fdtd_ctx *ctx, void *buf, size_t cap, size_t *size);
+int fdtd_load(fdtd_ctx *ctx, const void *buf, size_t size);
+
+/* Failure-detection self-test of the bounded device waits.  Launches one
+ * block on `stream` (NULL: the default stream) that waits on an mbarrier no
+ * one arrives at, with the fused kernel's bounded poll (max_polls polls,
+ * 0 = the fused kernel's limit).  The wait must give up and report it:
+ * returns FDTD_ETIMEOUT (the expected result), FDTD_OK if the wait did not
+ * time out, or FDTD_ECUDA.  Nothing faults, traps or hangs, and the device
+ * stays usable.  Allocates one int and frees it.  Synchronises. */
+int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls);
+
 /* Replace the material ids of the board (same eps_r table, PEC and ports),
  * copying host mat_ids [nz][ny][nx] to the device and rebuilding the edge
  * coefficient ids, then reset.  Returns FDTD_EINVAL if the new geometry has

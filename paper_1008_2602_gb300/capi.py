@@ -70,6 +70,9 @@ _SIGS = {
     "fdtd_reset": (c_int, [c_void_p]),
     "fdtd_set_materials": (c_int, [c_void_p, c_void_p]),
     "fdtd_info": (c_int, [c_void_p, P(fdtd_info_t)]),
+    "fdtd_save": (c_int, [c_void_p, c_void_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
+    "fdtd_selftest_wait_timeout": (c_int, [c_void_p, ctypes.c_uint]),
+    "fdtd_load": (c_int, [c_void_p, c_void_p, ctypes.c_size_t]),
     "fdtd_sync": (c_int, [c_void_p]),
     "fdtd_destroy": (None, [c_void_p]),
     "fdtd_strerror": (ctypes.c_char_p, [c_int]),

@@ -495,21 +495,38 @@ long long dft_items(const Board &h)
     return (long long)h.n_bins * ((h.n_probe + kDftProbeGroup - 1) / kDftProbeGroup);
 }
 
-// Lay out plan arrays [boards | int_prefix | zp_prefix | slab_prefix | dft_prefix | work] in buf.
+// Lay out plan arrays [boards | int_prefix | zp_prefix | slab_prefix | dft_prefix | work | slab blocks] in buf.
 int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long long *&buf, size_t &cap,
                Plan &plan, cudaStream_t st, std::vector<long long> &host)
 {
     const int nb = (int)boards.size();
-    const size_t words = (size_t)nb + 4 * ((size_t)nb + 1) + 1;   // + two work counters
+    long long n_slab_blk = 0;
+    for (int b = 0; b < nb; ++b) n_slab_blk += boards[b]->h.slab_blocks;
+    static_assert(sizeof(SlabBlock) == 4 * sizeof(long long), "slab block descriptor layout");
+    const size_t head = ((size_t)nb + 4 * ((size_t)nb + 1) + 1 + 1) & ~(size_t)1;   // + two work counters, 16-byte aligned
+    const size_t words = head + 4 * (size_t)n_slab_blk;
     host.assign(words, 0);
     long long *ptrs = host.data();
     long long *ip = ptrs + nb, *zp = ip + nb + 1, *sp = zp + nb + 1, *dp = sp + nb + 1;
+    SlabBlock *sb = reinterpret_cast<SlabBlock *>(ptrs + head);
     for (int b = 0; b < nb; ++b) {
+        const Board &h = boards[b]->h;
         ptrs[b] = (long long)(uintptr_t)boards[b]->d;
-        ip[b + 1] = ip[b] + fused_items(boards[b]->h, t, false);
-        zp[b + 1] = zp[b] + fused_items(boards[b]->h, t, true);
-        sp[b + 1] = sp[b] + boards[b]->h.slab_blocks;
-        dp[b + 1] = dp[b] + dft_items(boards[b]->h);
+        ip[b + 1] = ip[b] + fused_items(h, t, false);
+        zp[b + 1] = zp[b] + fused_items(h, t, true);
+        sp[b + 1] = sp[b] + h.slab_blocks;
+        dp[b + 1] = dp[b] + dft_items(h);
+        for (int s = 0; s < h.n_slab; ++s) {
+            const int end = s + 1 < h.n_slab ? (int)h.slab[s + 1].block0 : h.slab_blocks;
+            for (int k = (int)h.slab[s].block0; k < end; ++k) {
+                SlabBlock &e = sb[sp[b] + k];
+                e.B = boards[b]->d;
+                e.step = h.step;
+                e.stop = h.stop;
+                e.slab = s;
+                e.t0 = (k - (int)h.slab[s].block0) * kSlabThreads;
+            }
+        }
     }
     if (words > cap) {
         if (buf) cudaFree(buf);
@@ -537,6 +554,7 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.n_slab = sp[nb];
     plan.n_dft = dp[nb];
     plan.work = (int *)(buf + nb + 4 * (nb + 1));
+    plan.slab_blk = reinterpret_cast<const SlabBlock *>(buf + head);
     return FDTD_OK;
 }
 
@@ -1087,6 +1105,134 @@ int fdtd_reset(fdtd_ctx *c)
     CK(cudaMemsetAsync(h.dft_done, 0, sizeof(long long), c->cur));
     CK(cudaMemsetAsync(h.status, 0, sizeof(int), c->cur));
     c->host_step = 0;
+    return FDTD_OK;
+}
+
+namespace {
+
+// Checkpoint header: identifies the board the state belongs to.
+struct CkptHeader {
+    uint64_t magic;
+    int32_t version;
+    int32_t nx, ny, nz, pitch, prec, n_probe, n_src, n_total, n_bins, n_slab;
+    float scale;
+    int32_t pad;
+    int64_t nodes, step, dft_done;
+    double dt;
+};
+constexpr uint64_t kCkptMagic = 0x31544b43445446ull;   // "FDTDCKT1"
+
+// Device regions of the state, in checkpoint order.
+void ckpt_regions(const fdtd_ctx *c, std::vector<std::pair<void *, size_t>> &out)
+{
+    const Board &h = c->h;
+    const size_t fbytes = (size_t)h.nodes * elem_size(c->prec);
+    for (int p = 0; p < 2; ++p)
+        for (int f = 0; f < 6; ++f) out.push_back({h.f[p][f], fbytes});
+    for (int s = 0; s < h.n_slab; ++s)
+        for (int a = 0; a < 6; ++a)
+            if (h.slab[s].aux[a]) out.push_back({h.slab[s].aux[a], sizeof(float) * (size_t)h.slab[s].n});
+    for (int bx = 0; bx < 2; ++bx) {
+        if (h.zD[bx]) out.push_back({h.zD[bx], sizeof(float) * c->zaux_n[bx]});
+        for (int p = 0; p < 2; ++p)
+            if (h.zB[bx][p]) out.push_back({h.zB[bx][p], sizeof(float) * c->zaux_n[bx]});
+    }
+    if (h.trace) out.push_back({h.trace, sizeof(float) * (size_t)h.n_probe * h.n_total});
+    if (h.dft) out.push_back({h.dft, sizeof(double) * 2 * (size_t)h.n_probe * std::max(h.n_bins, 1)});
+}
+
+CkptHeader ckpt_header(const fdtd_ctx *c)
+{
+    const Board &h = c->h;
+    CkptHeader H{};
+    H.magic = kCkptMagic;
+    H.version = 1;
+    H.nx = h.nx; H.ny = h.ny; H.nz = h.nz; H.pitch = h.pitch; H.prec = c->prec;
+    H.n_probe = (int)c->probe.size(); H.n_src = (int)c->src.size();
+    H.n_total = h.n_total; H.n_bins = h.n_bins; H.n_slab = h.n_slab;
+    H.scale = h.scale;
+    H.nodes = h.nodes;
+    H.dt = c->dt;
+    return H;
+}
+
+}  // namespace
+
+int fdtd_save(fdtd_ctx *c, void *buf, size_t cap, size_t *size)
+{
+    if (!c || !size) return fail(FDTD_EINVAL, "NULL argument");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; remove it first");
+    if (int r = finalize(c)) return r;
+    std::vector<std::pair<void *, size_t>> reg;
+    ckpt_regions(c, reg);
+    size_t need = sizeof(CkptHeader);
+    for (auto &g : reg) need += g.second;
+    *size = need;
+    if (!buf || cap < need) return FDTD_OK;
+    CkptHeader H = ckpt_header(c);
+    long long ctr[2] = {0, 0};
+    CK(cudaMemcpyAsync(&ctr[0], c->h.step, sizeof(long long), cudaMemcpyDeviceToHost, c->cur));
+    CK(cudaMemcpyAsync(&ctr[1], c->h.dft_done, sizeof(long long), cudaMemcpyDeviceToHost, c->cur));
+    unsigned char *o = static_cast<unsigned char *>(buf) + sizeof(CkptHeader);
+    for (auto &g : reg) {
+        CK(cudaMemcpyAsync(o, g.first, g.second, cudaMemcpyDeviceToHost, c->cur));
+        o += g.second;
+    }
+    CK(cudaStreamSynchronize(c->cur));
+    H.step = ctr[0];
+    H.dft_done = ctr[1];
+    std::memcpy(buf, &H, sizeof(H));
+    return check_status(c);
+}
+
+int fdtd_load(fdtd_ctx *c, const void *buf, size_t size)
+{
+    if (!c || !buf) return fail(FDTD_EINVAL, "NULL argument");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; remove it first");
+    if (size < sizeof(CkptHeader)) return fail(FDTD_EINVAL, "checkpoint too small");
+    if (int r = finalize(c)) return r;
+    CkptHeader H;
+    std::memcpy(&H, buf, sizeof(H));
+    const CkptHeader M = ckpt_header(c);
+    if (H.magic != kCkptMagic || H.version != M.version) return fail(FDTD_EINVAL, "not an fdtd checkpoint");
+    if (H.nx != M.nx || H.ny != M.ny || H.nz != M.nz || H.pitch != M.pitch || H.prec != M.prec ||
+        H.n_probe != M.n_probe || H.n_src != M.n_src || H.n_total != M.n_total || H.n_bins != M.n_bins ||
+        H.n_slab != M.n_slab || H.scale != M.scale || H.nodes != M.nodes || H.dt != M.dt)
+        return fail(FDTD_EINVAL, "checkpoint belongs to a different board or settings");
+    if (H.step < 0 || H.dft_done < 0 || H.dft_done > H.step) return fail(FDTD_EINVAL, "corrupt checkpoint counters");
+    std::vector<std::pair<void *, size_t>> reg;
+    ckpt_regions(c, reg);
+    size_t need = sizeof(CkptHeader);
+    for (auto &g : reg) need += g.second;
+    if (size != need) return fail(FDTD_EINVAL, "checkpoint size does not match this board");
+    const unsigned char *in = static_cast<const unsigned char *>(buf) + sizeof(CkptHeader);
+    for (auto &g : reg) {
+        CK(cudaMemcpyAsync(g.first, in, g.second, cudaMemcpyHostToDevice, c->cur));
+        in += g.second;
+    }
+    const long long ctr[2] = {H.step, H.dft_done};
+    CK(cudaMemcpyAsync(c->h.step, &ctr[0], sizeof(long long), cudaMemcpyHostToDevice, c->cur));
+    CK(cudaMemcpyAsync(c->h.dft_done, &ctr[1], sizeof(long long), cudaMemcpyHostToDevice, c->cur));
+    CK(cudaMemsetAsync(c->h.status, 0, sizeof(int), c->cur));
+    CK(cudaStreamSynchronize(c->cur));
+    c->host_step = H.step;
+    return FDTD_OK;
+}
+
+int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls)
+{
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(int));
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(FDTD_ECUDA, "selftest allocation failed"); }
+    int status = 0;
+    e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = launch_wait_selftest(d, max_polls ? max_polls : (1u << 21), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return cuda_fail(e, "selftest");
+    if (status & 2) return fail(FDTD_ETIMEOUT, "bounded device wait gave up (self-test: expected)");
     return FDTD_OK;
 }
 

@@ -129,6 +129,16 @@ struct Board {
     int pad1;
 };
 
+// One slab-kernel block of a plan: everything its threads need to start
+// loading, so a block's set-up is one table read plus loads that do not
+// depend on one another.
+struct SlabBlock {
+    const Board *B;
+    const long long *step, *stop;   // the board's step counters
+    int slab;                       // slab index within the board
+    int t0;                         // first slab-local thread of the block
+};
+
 // A launch plan over one or more boards: per-phase work-item prefix sums.
 struct Plan {
     int nb;
@@ -137,6 +147,7 @@ struct Plan {
     const long long *int_prefix;  // [nb + 1] interior-kernel items (planes [iz0, iz1))
     const long long *zp_prefix;   // [nb + 1] z-UPML-kernel items (planes [1, iz0) and [iz1, nz))
     const long long *slab_prefix; // [nb + 1] slab blocks
+    const SlabBlock *slab_blk;    // [n_slab] per-block descriptors
     const long long *dft_prefix;  // [nb + 1] DFT warps
     long long n_int, n_zp, n_slab, n_dft;
     int *work;                    // fused-kernel work counters [interior, z-UPML] (zeroed before every launch)
@@ -158,7 +169,7 @@ __host__ __device__ constexpr int box_c16(int tx) { return box_up(tx + 7, 8); }
 __host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 5, 4); }
 
 constexpr int kSlabThreads = 256;
-constexpr int kSlabKz = 4;          // planes per slab-kernel thread
+constexpr int kSlabKz = 8;          // planes per slab-kernel thread
 constexpr int kDftProbeGroup = 4;
 
 enum Phase : int { kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseInterior = 2, kPhaseSlabE = 3, kPhasePost = 4, kNumPhases = 5 };
@@ -175,5 +186,6 @@ bool fused_tile_supported(int tile_x, int tile_y);
 // Record the message returned by fdtd_last_error on this thread; returns code.
 int set_error(int code, const char *msg);
 cudaError_t fused_set_smem_limits();
+cudaError_t launch_wait_selftest(int *status, unsigned max_polls, cudaStream_t st);
 
 }  // namespace fdtd

@@ -68,6 +68,13 @@ __device__ __forceinline__ bool board_active(const Board *B)
     return *((volatile long long *)B->step) < *((volatile long long *)B->stop);
 }
 
+// The step counters as seen by the field kernels: written only by other
+// launches (k_post, the host's stop updates), so within one launch they are
+// read-only and every warp may read them through the cached read-only path
+// (a per-warp L2 read of one shared line would serialise on that line).
+__device__ __forceinline__ long long step_ro(const Board *B) { return __ldg(B->step); }
+__device__ __forceinline__ bool active_ro(const Board *B) { return __ldg(B->step) < __ldg(B->stop); }
+
 // ------------------------------------------------------------------ fused region
 // H~^{n+1/2} components at node q straight from global memory (input parity);
 // used once per z-segment for the plane below the segment.
@@ -77,6 +84,7 @@ struct Fields {
     const T *__restrict__ hx, *__restrict__ hy, *__restrict__ hz;
     T *__restrict__ oex, *__restrict__ oey, *__restrict__ oez;
     T *__restrict__ ohx, *__restrict__ ohy, *__restrict__ ohz;
+    Fields() = default;
     __device__ __forceinline__ Fields(const Board *B, int par)
     {
         ex = (const T *)B->f[par][0]; ey = (const T *)B->f[par][1]; ez = (const T *)B->f[par][2];
@@ -179,10 +187,11 @@ __device__ __forceinline__ bool mbar_try(uint64_t *b, uint32_t parity)
 }
 // Bounded wait on a phase: gives up after ~2^21 polls (each poll itself
 // suspends for a hardware-defined slice) and reports it in *status.
-__device__ __forceinline__ void mbar_wait(uint64_t *b, uint32_t parity, int *status, int *abort_flag)
+__device__ __forceinline__ void mbar_wait(uint64_t *b, uint32_t parity, int *status, int *abort_flag,
+                                          uint32_t max_polls = 1u << 21)
 {
     if (*(volatile int *)abort_flag) return;
-    for (uint32_t it = 0; it < (1u << 21); ++it)
+    for (uint32_t it = 0; it < max_polls; ++it)
         if (mbar_try(b, parity)) return;
     atomicOr(status, 2);
     *(volatile int *)abort_flag = 1;
@@ -360,8 +369,8 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
     const long long *prefix = ZP ? plan.zp_prefix : plan.int_prefix;
     const int b = find_board(prefix, plan.nb, item);
     t.B = plan.boards[b];
-    t.ok = board_active(t.B);
-    const long long step = *((volatile long long *)t.B->step);
+    t.ok = active_ro(t.B);
+    const long long step = step_ro(t.B);
     t.par = (int)(step & 1);
     const long long local = item - __ldg(prefix + b);
     constexpr int TX = kWarpCols * W;
@@ -717,27 +726,41 @@ struct SlabCol {
     int i, j, kbeg, kend;
 };
 
-__device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, const Board *&B, SlabCol &sc)
+// Block set-up from the plan's per-block descriptor: the step counters, the
+// slab's box and both parities' field pointers are independent loads.
+template <typename T>
+__device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, const Board *&B, SlabCol &sc,
+                                            Fields<T> &F)
 {
-    const int b = find_board(plan.slab_prefix, plan.nb, blk);
-    B = plan.boards[b];
-    if (!board_active(B)) return false;
-    const int lb = (int)(blk - __ldg(plan.slab_prefix + b));
-    int s = 0;
-    while (s + 1 < B->n_slab && B->slab[s + 1].block0 <= lb) ++s;
-    const Slab *sl = &B->slab[s];
-    const int ni = sl->ni, nij = ni * sl->nj;
-    const int nkz = (sl->k1 - sl->k0 + kSlabKz - 1) / kSlabKz;
-    const int tt = (lb - (int)sl->block0) * kSlabThreads + (int)threadIdx.x;
+    const SlabBlock d = plan.slab_blk[blk];
+    B = d.B;
+    const long long step = __ldg(d.step), stop = __ldg(d.stop);
+    const Slab *sl = &B->slab[d.slab];
+    const int ni = sl->ni, nj = sl->nj, i0 = sl->i0, j0 = sl->j0, k0 = sl->k0, k1 = sl->k1;
+    const void *f0[6], *f1[6];
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+        f0[c] = B->f[0][c];
+        f1[c] = B->f[1][c];
+    }
+    if (step >= stop) return false;
+    const int nij = ni * nj;
+    const int nkz = (k1 - k0 + kSlabKz - 1) / kSlabKz;
+    const int tt = d.t0 + (int)threadIdx.x;
     if (tt >= nij * nkz) return false;
+    const bool p1 = (step & 1) != 0;
+    F.ex = (const T *)(p1 ? f1[0] : f0[0]); F.ey = (const T *)(p1 ? f1[1] : f0[1]); F.ez = (const T *)(p1 ? f1[2] : f0[2]);
+    F.hx = (const T *)(p1 ? f1[3] : f0[3]); F.hy = (const T *)(p1 ? f1[4] : f0[4]); F.hz = (const T *)(p1 ? f1[5] : f0[5]);
+    F.oex = (T *)(p1 ? f0[0] : f1[0]); F.oey = (T *)(p1 ? f0[1] : f1[1]); F.oez = (T *)(p1 ? f0[2] : f1[2]);
+    F.ohx = (T *)(p1 ? f0[3] : f1[3]); F.ohy = (T *)(p1 ? f0[4] : f1[4]); F.ohz = (T *)(p1 ? f0[5] : f1[5]);
     const int kz = tt / nij, ij = tt - kz * nij;
     const int jj = ij / ni;
     sc.sl = sl;
     sc.nij = nij;
-    sc.i = sl->i0 + (ij - jj * ni);
-    sc.j = sl->j0 + jj;
-    sc.kbeg = sl->k0 + kz * kSlabKz;
-    sc.kend = min(sc.kbeg + kSlabKz, sl->k1);
+    sc.i = i0 + (ij - jj * ni);
+    sc.j = j0 + jj;
+    sc.kbeg = k0 + kz * kSlabKz;
+    sc.kend = min(sc.kbeg + kSlabKz, k1);
     sc.t = (long long)kz * kSlabKz * nij + ij;
     return true;
 }
@@ -780,9 +803,8 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
         SlabCol sc;
-        if (!slab_locate(plan, blk, B, sc)) continue;
-        const long long step = *((volatile long long *)B->step);
-        const Fields<T> F(B, (int)(step & 1));
+        Fields<T> F;
+        if (!slab_locate(plan, blk, B, sc, F)) continue;
         const int i = sc.i, j = sc.j, nz = B->nz;
         const int X = B->pitch;
         const long long P = B->plane;
@@ -848,9 +870,8 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
         SlabCol sc;
-        if (!slab_locate(plan, blk, B, sc)) continue;
-        const long long step = *((volatile long long *)B->step);
-        const Fields<T> F(B, (int)(step & 1));
+        Fields<T> F;
+        if (!slab_locate(plan, blk, B, sc, F)) continue;
         const int i = sc.i, j = sc.j;
         const int nx = B->nx, ny = B->ny, nz = B->nz;
         const int X = B->pitch;
@@ -1096,6 +1117,29 @@ __global__ void k_energy_final(const double *partials, int n, double *out2)
     }
 }
 
+// ------------------------------------------------------------------ failure detection
+// Self-test of the bounded wait: an mbarrier that nothing arrives on, waited
+// on with the same bounded poll as the fused kernel, must give up, set
+// status bit 1 (value 2) and return, leaving the context usable.
+__global__ void k_wait_selftest(int *status, uint32_t max_polls)
+{
+    __shared__ uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, status, &abort_flag, max_polls);
+}
+
+cudaError_t launch_wait_selftest(int *status, unsigned max_polls, cudaStream_t st)
+{
+    k_wait_selftest<<<1, 32, 0, st>>>(status, max_polls);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ launchers
 // Fused-kernel configurations: W compute warps x 62 columns by TY rows, an
 // NS-stage ring; ZP selects the z-UPML launch.
@@ -1144,13 +1188,16 @@ static void launch_fused(const Plan &plan, cudaStream_t st)
     }
 }
 
+// Slab kernels launch one block per descriptor (grid-striding past this).
+constexpr long long kMaxGrid = 1 << 20;
+
 template <typename T>
 static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream_t st)
 {
     switch (phase) {
     case kPhaseSlabH:
         if (plan.n_slab > 0)
-            k_slab_h<T><<<(int)(plan.n_slab < grid_cap ? plan.n_slab : grid_cap), kSlabThreads, 0, st>>>(plan);
+            k_slab_h<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, 0, st>>>(plan);
         break;
     case kPhaseFusedZ:
         if (plan.n_zp > 0) {
@@ -1166,7 +1213,7 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
         break;
     case kPhaseSlabE:
         if (plan.n_slab > 0)
-            k_slab_e<T><<<(int)(plan.n_slab < grid_cap ? plan.n_slab : grid_cap), kSlabThreads, 0, st>>>(plan);
+            k_slab_e<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, 0, st>>>(plan);
         break;
     default:
         k_post<T><<<plan.nb, 128, 0, st>>>(plan);

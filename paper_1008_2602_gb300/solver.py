@@ -123,6 +123,20 @@ class Solver:
             C.fdtd_probe_trace(self.ctx, p, out[p].ctypes.data, n, ctypes.byref(ln))
         return out[:, : ln.value] if inf["n_probes"] else out
 
+    def save(self) -> bytes:
+        """Checkpoint of the whole solver state (fdtd_save)."""
+        n = ctypes.c_size_t()
+        C.fdtd_save(self.ctx, None, 0, ctypes.byref(n))
+        buf = ctypes.create_string_buffer(n.value)
+        C.fdtd_save(self.ctx, buf, n.value, ctypes.byref(n))
+        return buf.raw
+
+    def load(self, state: bytes) -> "Solver":
+        """Restore a checkpoint taken from a solver of the same problem (fdtd_load)."""
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        C.fdtd_load(self.ctx, buf, len(state))
+        return self
+
     def field(self, comp: int) -> np.ndarray:
         p = self.problem
         out = np.zeros((p.nz + 1, p.ny + 1, p.nx + 1), dtype=np.float32)

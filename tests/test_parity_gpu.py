@@ -291,3 +291,36 @@ def test_autotuner_picks_a_valid_configuration(fdtd, tmp_path, monkeypatch):
     assert np.array_equal(a.field(2), b.field(2))
     assert tune.tune(probs, steps=6) == cfg   # cached
     a.close(); b.close()
+
+
+def test_checkpoint_resume_is_bitwise(fdtd):
+    """Run N steps = run k steps, save, load into a fresh solver of the same
+    problem, run N - k: fields and traces bitwise equal, spectra equal to
+    FP64 rounding (the running DFT folds samples at chunk boundaries, which
+    differ between the two runs); a checkpoint of another board is refused
+    and leaves the solver unchanged."""
+    p = W.random_problem(21, 40, 30, 20, upml=4, n_steps=300)
+    ref = fdtd.Solver(p)
+    ref.run()
+    a = fdtd.Solver(p)
+    a.step(137)
+    state = a.save()
+    a.close()
+    b = fdtd.Solver(p)
+    b.load(state)
+    assert b.info()["step"] == 137
+    b.step(300 - 137)
+    for c in range(6):
+        assert np.array_equal(b.field(c), ref.field(c)), c
+    assert np.array_equal(b.traces(), ref.traces())
+    sp, sr = b.spectra(), ref.spectra()
+    assert np.allclose(sp, sr, rtol=0, atol=1e-12 * np.abs(sr).max())
+    assert b.diagnostics() == ref.diagnostics()
+    other = fdtd.Solver(W.random_problem(22, 41, 30, 20, upml=4, n_steps=300))
+    from paper_1008_2602_gb300 import capi
+    with pytest.raises(capi.FdtdError) as ei:
+        other.load(state)
+    assert ei.value.code == capi.FDTD_EINVAL
+    assert other.info()["step"] == 0
+    for s in (ref, b, other):
+        s.close()
