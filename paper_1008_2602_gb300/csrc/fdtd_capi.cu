@@ -806,7 +806,9 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
         sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
         sl.block0 = blocks;
-        const long long cols = (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
+        // threads: (i, j) columns marching z, or (i, k) columns marching y for a single plane
+        const long long cols = sl.k1 - sl.k0 == 1 ? (long long)sl.ni * ((sl.nj + kSlabKz - 1) / kSlabKz)
+                                                  : (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
         blocks += (int)((cols + kSlabThreads - 1) / kSlabThreads);
         const int lo[3] = {sl.i0, sl.j0, sl.k0}, hi[3] = {sl.i1, sl.j1, sl.k1};
         auto any_nontrivial = [&](int axis, int half, bool need_b1g, bool need_apam) {

@@ -64,7 +64,8 @@ struct Slab {
     int ni, nj;                   // i1 - i0, j1 - j0
     long long n;                  // nodes in the box
     long long block0;             // first slab-kernel block of this slab (board-local)
-                                  // (blocks cover ni * nj * ceil(nk / kSlabKz) threads)
+                                  // (blocks cover ni * nj * ceil(nk / kSlabKz) threads, or
+                                  // ni * ceil(nj / kSlabKz) for a single plane)
     float *aux[6];                // D~x, D~y, D~z, B~x, B~y, B~z or nullptr
 };
 

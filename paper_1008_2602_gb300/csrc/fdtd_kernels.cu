@@ -716,14 +716,17 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
 }
 
 // ------------------------------------------------------------------ slabs
-// A slab thread owns one (i, j) column of its slab for kSlabKz consecutive
-// planes: consecutive threads take consecutive i (coalesced rows), and the
-// per-column UPML factors and index arithmetic are paid once per column.
+// A slab thread marches kSlabKz consecutive nodes of its slab: along z for
+// slabs more than one plane thick (an (i, j) column), along y for the two
+// single-plane z slabs (an (i, k) column).  Consecutive threads take
+// consecutive i, so rows are coalesced, and the per-column UPML factors and
+// index arithmetic are paid once per column.
 struct SlabCol {
     const Slab *sl;
-    long long t;          // slab-local (aux) index of (i, j, kbeg); + nij per plane
-    int nij;
-    int i, j, kbeg, kend;
+    long long t;          // slab-local (aux) index of the first node; + tstep per node
+    int tstep;
+    bool ym;              // marching along y (else z)
+    int i, j, k, count;   // first node, nodes to march
 };
 
 // Block set-up from the plan's per-block descriptor: the step counters, the
@@ -736,7 +739,7 @@ __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, con
     B = d.B;
     const long long step = __ldg(d.step), stop = __ldg(d.stop);
     const Slab *sl = &B->slab[d.slab];
-    const int ni = sl->ni, nj = sl->nj, i0 = sl->i0, j0 = sl->j0, k0 = sl->k0, k1 = sl->k1;
+    const int ni = sl->ni, nj = sl->nj, i0 = sl->i0, j0 = sl->j0, k0 = sl->k0, k1 = sl->k1, j1 = sl->j1;
     const void *f0[6], *f1[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
@@ -744,24 +747,38 @@ __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, con
         f1[c] = B->f[1][c];
     }
     if (step >= stop) return false;
+    const bool ym = (k1 - k0 == 1);
     const int nij = ni * nj;
-    const int nkz = (k1 - k0 + kSlabKz - 1) / kSlabKz;
     const int tt = d.t0 + (int)threadIdx.x;
-    if (tt >= nij * nkz) return false;
+    if (ym) {
+        const int nrow = (nj + kSlabKz - 1) / kSlabKz;
+        if (tt >= ni * nrow) return false;
+        const int jr = tt / ni, ii = tt - jr * ni;
+        sc.i = i0 + ii;
+        sc.j = j0 + jr * kSlabKz;
+        sc.k = k0;
+        sc.count = min(kSlabKz, j1 - sc.j);
+        sc.t = (long long)jr * kSlabKz * ni + ii;
+        sc.tstep = ni;
+    } else {
+        const int nkz = (k1 - k0 + kSlabKz - 1) / kSlabKz;
+        if (tt >= nij * nkz) return false;
+        const int kz = tt / nij, ij = tt - kz * nij;
+        const int jj = ij / ni;
+        sc.i = i0 + (ij - jj * ni);
+        sc.j = j0 + jj;
+        sc.k = k0 + kz * kSlabKz;
+        sc.count = min(kSlabKz, k1 - sc.k);
+        sc.t = (long long)kz * kSlabKz * nij + ij;
+        sc.tstep = nij;
+    }
+    sc.ym = ym;
+    sc.sl = sl;
     const bool p1 = (step & 1) != 0;
     F.ex = (const T *)(p1 ? f1[0] : f0[0]); F.ey = (const T *)(p1 ? f1[1] : f0[1]); F.ez = (const T *)(p1 ? f1[2] : f0[2]);
     F.hx = (const T *)(p1 ? f1[3] : f0[3]); F.hy = (const T *)(p1 ? f1[4] : f0[4]); F.hz = (const T *)(p1 ? f1[5] : f0[5]);
     F.oex = (T *)(p1 ? f0[0] : f1[0]); F.oey = (T *)(p1 ? f0[1] : f1[1]); F.oez = (T *)(p1 ? f0[2] : f1[2]);
     F.ohx = (T *)(p1 ? f0[3] : f1[3]); F.ohy = (T *)(p1 ? f0[4] : f1[4]); F.ohz = (T *)(p1 ? f0[5] : f1[5]);
-    const int kz = tt / nij, ij = tt - kz * nij;
-    const int jj = ij / ni;
-    sc.sl = sl;
-    sc.nij = nij;
-    sc.i = i0 + (ij - jj * ni);
-    sc.j = j0 + jj;
-    sc.kbeg = k0 + kz * kSlabKz;
-    sc.kend = min(sc.kbeg + kSlabKz, k1);
-    sc.t = (long long)kz * kSlabKz * nij + ij;
     return true;
 }
 
@@ -805,27 +822,32 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
         SlabCol sc;
         Fields<T> F;
         if (!slab_locate(plan, blk, B, sc, F)) continue;
-        const int i = sc.i, j = sc.j, nz = B->nz;
+        const int i = sc.i, ny = B->ny, nz = B->nz;
         const int X = B->pitch;
         const long long P = B->plane;
         const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
         const Slab &sl = *sc.sl;
         float *const ax = sl.aux[3], *const ay = sl.aux[4], *const az = sl.aux[5];
-        const bool xin = i < B->nx, yin = j < B->ny;
-        const int di = xin ? 1 : 0, dj = yin ? X : 0;   // clamped +x, +y neighbour offsets
-        // factors fixed along the column: H_x (y half, x integer), H_y (x half,
-        // y integer), H_z (x half, y half)
-        const Coef y1 = B->cw[1][1][j], x0 = B->cw[0][0][i], x1 = B->cw[0][1][i], y0 = B->cw[1][0][j];
-        long long idx = (long long)sc.kbeg * P + (long long)j * X + i;
+        const bool xin = i < B->nx;
+        const int di = xin ? 1 : 0;   // clamped +x neighbour offset
+        // x factors fixed along the column: H_x (x integer), H_y, H_z (x half)
+        const Coef x0 = B->cw[0][0][i], x1 = B->cw[0][1][i];
+        int j = sc.j, k = sc.k;
+        long long idx = (long long)k * P + (long long)j * X + i;
         long long t = sc.t;
-        // E_y, E_x of the current plane; the (k+1) loads become the next plane's
+        const long long didx = sc.ym ? X : P;
+        // E_y, E_x of the current node; marching z, the (k+1) loads become the next node's
         float eyc = Io<T>::ld(F.ey + idx);
         float exc = Io<T>::ld(F.ex + idx);
 #pragma unroll
         for (int m = 0; m < kSlabKz; ++m) {
-            const int k = sc.kbeg + m;
-            if (k >= sc.kend) break;
-            const bool zin = k < nz;
+            if (m >= sc.count) break;
+            if (sc.ym && m > 0) {
+                eyc = Io<T>::ld(F.ey + idx);
+                exc = Io<T>::ld(F.ex + idx);
+            }
+            const bool yin = j < ny, zin = k < nz;
+            const int dj = yin ? X : 0;   // clamped +y, +z neighbour offsets
             const long long dk = zin ? P : 0;
             const float eyu = Io<T>::ld(F.ey + idx + dk), exu = Io<T>::ld(F.ex + idx + dk);
             const float ezc = Io<T>::ld(F.ez + idx);
@@ -833,7 +855,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
             const float eyi = Io<T>::ld(F.ey + idx + di), exj = Io<T>::ld(F.ex + idx + dj);
             const float hxo = Io<T>::ld(F.hx + idx), hyo = Io<T>::ld(F.hy + idx), hzo = Io<T>::ld(F.hz + idx);
             const float bxo = ax ? ax[t] : 0.f, byo = ay ? ay[t] : 0.f, bzo = az ? az[t] : 0.f;
-            const Coef z1 = B->cw[2][1][k], z0 = B->cw[2][0][k];
+            const Coef y1 = B->cw[1][1][j], y0 = B->cw[1][0][j], z1 = B->cw[2][1][k], z0 = B->cw[2][0][k];
             float bn;
             if (yin && zin) {   // H_x(i, j+1/2, k+1/2)
                 const float h = upml_h2(hxo, curl2(ezj, ezc, eyu, eyc, Sy, Sz), y1, z1, x0, ax != nullptr, bxo, bn);
@@ -852,8 +874,9 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
             }
             eyc = eyu;
             exc = exu;
-            idx += P;
-            t += sc.nij;
+            idx += didx;
+            t += sc.tstep;
+            if (sc.ym) ++j; else ++k;
         }
     }
 }
@@ -872,7 +895,7 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
         SlabCol sc;
         Fields<T> F;
         if (!slab_locate(plan, blk, B, sc, F)) continue;
-        const int i = sc.i, j = sc.j;
+        const int i = sc.i;
         const int nx = B->nx, ny = B->ny, nz = B->nz;
         const int X = B->pitch;
         const long long P = B->plane;
@@ -880,25 +903,26 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
         const Slab &sl = *sc.sl;
         float *const ax = sl.aux[0], *const ay = sl.aux[1], *const az = sl.aux[2];
         const int *w = B->wall;
-        // images across the x and y walls (fixed along the column)
-        const bool xhi = i == nx, xlo = i == 0, yhi = j == ny, ylo = j == 0;
-        const float sxh = hsign(xhi, w[1]), sxl = hsign(xlo, w[0]), syh = hsign(yhi, w[3]), syl = hsign(ylo, w[2]);
+        const int w2 = w[2], w3 = w[3], w4 = w[4], w5 = w[5];
+        // images across the x walls (fixed along the column)
+        const bool xhi = i == nx, xlo = i == 0;
+        const float sxh = hsign(xhi, w[1]), sxl = hsign(xlo, w[0]);
         const int ox1 = xhi ? -1 : 0, ox0 = xlo ? 0 : -1;   // offsets of H at i and i-1 (or images)
-        const int oy1 = yhi ? -X : 0, oy0 = ylo ? 0 : -X;
-        // factors fixed along the column: E_x (y integer, x half), E_y (x
-        // integer, y half), E_z (x integer, y integer)
-        const Coef y0 = B->cw[1][0][j], x1 = B->cw[0][1][i], x0 = B->cw[0][0][i], y1 = B->cw[1][1][j];
-        long long idx = (long long)sc.kbeg * P + (long long)j * X + i;
+        // x factors fixed along the column: E_x (x half), E_y, E_z (x integer)
+        const Coef x1 = B->cw[0][1][i], x0 = B->cw[0][0][i];
+        int j = sc.j, k = sc.k;
+        long long idx = (long long)k * P + (long long)j * X + i;
         long long t = sc.t;
+        const long long didx = sc.ym ? X : P;
 #pragma unroll
         for (int m = 0; m < kSlabKz; ++m) {
-            const int k = sc.kbeg + m;
-            if (k >= sc.kend) break;
-            const bool zhi = k == nz, zlo = k == 0;
-            const float szh = hsign(zhi, w[5]), szl = hsign(zlo, w[4]);
+            if (m >= sc.count) break;
+            const bool yhi = j == ny, ylo = j == 0, zhi = k == nz, zlo = k == 0;
+            const float syh = hsign(yhi, w3), syl = hsign(ylo, w2), szh = hsign(zhi, w5), szl = hsign(zlo, w4);
+            const int oy1 = yhi ? -X : 0, oy0 = ylo ? 0 : -X;
             const long long oz1 = zhi ? -P : 0, oz0 = zlo ? 0 : -P;
             const float4 ce = __ldg(B->ctab + cid_at(B, idx));
-            const Coef z0 = B->cw[2][0][k], z1 = B->cw[2][1][k];
+            const Coef y0 = B->cw[1][0][j], y1 = B->cw[1][1][j], z0 = B->cw[2][0][k], z1 = B->cw[2][1][k];
             // H~ at the node and its -x, -y, -z neighbours (or their images)
             const float hz_y1 = syh * Io<T>::ld(F.ohz + idx + oy1), hz_y0 = syl * Io<T>::ld(F.ohz + idx + oy0);
             const float hy_z1 = szh * Io<T>::ld(F.ohy + idx + oz1), hy_z0 = szl * Io<T>::ld(F.ohy + idx + oz0);
@@ -927,8 +951,9 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
                 Io<T>::st(F.oez + idx, e);
                 if (az) az[t] = dn;
             }
-            idx += P;
-            t += sc.nij;
+            idx += didx;
+            t += sc.tstep;
+            if (sc.ym) ++j; else ++k;
         }
     }
 }
