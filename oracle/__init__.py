@@ -40,6 +40,7 @@ class _Problem(ctypes.Structure):
         ("src", ctypes.c_void_p), ("src_prm", ctypes.c_void_p), ("n_src", ctypes.c_int),
         ("probe", ctypes.c_void_p), ("n_probe", ctypes.c_int),
         ("n_steps", ctypes.c_int), ("n_bins", ctypes.c_int), ("n_threads", ctypes.c_int),
+        ("vsrc", ctypes.c_void_p), ("vsrc_prm", ctypes.c_void_p), ("n_vsrc", ctypes.c_int),
     ]
 
 
@@ -48,6 +49,7 @@ class _Outputs(ctypes.Structure):
         ("dt", ctypes.c_double),
         ("trace", ctypes.c_void_p), ("dft", ctypes.c_void_p), ("energy", ctypes.c_void_p),
         ("divb", ctypes.c_void_p), ("src_wave", ctypes.c_void_p), ("fields", ctypes.c_void_p),
+        ("vsrc_current", ctypes.c_void_p),
     ]
 
 
@@ -106,8 +108,8 @@ def n_bins(prob, dt: float) -> int:
 
 
 def run(prob, *, trace: bool = True, dft: bool = True, energy: bool = False, divb: bool = False,
-        src_wave: bool = False, fields: bool = False, n_threads: Optional[int] = None,
-        n_steps: Optional[int] = None) -> dict:
+        src_wave: bool = False, fields: bool = False, vsrc_current: bool = False,
+        n_threads: Optional[int] = None, n_steps: Optional[int] = None) -> dict:
     """Run the oracle on a ``workloads.Problem``; returns a dict of numpy arrays."""
     lib = _load()
     N = int(n_steps if n_steps is not None else prob.n_steps)
@@ -130,6 +132,10 @@ def run(prob, *, trace: bool = True, dft: bool = True, energy: bool = False, div
     P.walls[:] = list(prob.walls)
     P.src, P.src_prm, P.n_src = src.ctypes.data, prm.ctypes.data, len(src)
     P.probe, P.n_probe = prb.ctypes.data, len(prb)
+    vs = np.ascontiguousarray(getattr(prob, "vsources", np.zeros((0, 4))), dtype=np.int32).reshape(-1, 4)
+    vp = np.ascontiguousarray(getattr(prob, "vsource_params", np.zeros((0, 4))), dtype=np.float64).reshape(-1, 4)
+    assert len(vs) == len(vp)
+    P.vsrc, P.vsrc_prm, P.n_vsrc = vs.ctypes.data, vp.ctypes.data, len(vs)
     P.n_steps = N
     dt = prob.dt if prob.dt > 0 else prob.courant * cfl_dt(prob.dx, prob.dy, prob.dz)
     Q = n_bins(prob.replace(n_steps=N), dt) if dft else 0
@@ -141,6 +147,7 @@ def run(prob, *, trace: bool = True, dft: bool = True, energy: bool = False, div
         "trace": (trace, (len(prb), N)), "dft": (dft, (len(prb), Q, 2)),
         "energy": (energy, (N,)), "divb": (divb, (N,)), "src_wave": (src_wave, (N,)),
         "fields": (fields, (6, prob.nz + 1, prob.ny + 1, prob.nx + 1)),
+        "vsrc_current": (vsrc_current, (N,)),
     }
     for name, (want, shape) in bufs.items():
         if want:

@@ -27,6 +27,13 @@
  *    (tangential E = 0) or PMC (odd mirror of tangential H across the wall).
  *  - Current source (Eq. 8): J(t) = J0 ((t-t0)/tau) exp(-((t-t0)/tau)^2) at
  *    t = (n+1/2) dt on one E edge, entering Ampere's law as curl H - J.
+ *  - Resistive voltage source (Results section: V0 and Rs on one E edge, the
+ *    same pulse shape): a voltage Vs(t) in series with Rs across the edge of
+ *    length l and cross-section A = V/l.  Its current I = (l E + Vs)/Rs at
+ *    n+1/2, with E^{n+1/2} = (E^n + E^{n+1})/2, enters Ampere's law as
+ *    curl H - I/A, which is solved for E^{n+1} at that edge (so Vs is the
+ *    open-circuit voltage of the edge's lower node over its upper one:
+ *    E = -Vs/l when no current flows).  Edges must lie outside the UPML.
  *  - Probes sample E^{n+1}; running DFT X(f_q) = dt sum_n x^n exp(-j 2 pi q n/N)
  *    in FP64 (Results section: FFT of the ground-plane E_z).
  *  - Diagnostics: discrete energy W^n = 1/2 V (sum eps E^n.E^n +
@@ -76,6 +83,9 @@ typedef struct {
     int n_steps;
     int n_bins;
     int n_threads;
+    const int32_t *vsrc;            /* [n_vsrc][4] i,j,k,comp */
+    const double *vsrc_prm;         /* [n_vsrc][4] V0 [V], t0, tau [s], Rs [ohm] */
+    int n_vsrc;
 } oracle_problem;
 
 typedef struct {
@@ -86,6 +96,7 @@ typedef struct {
     double *divb;                   /* [n_steps] or NULL */
     double *src_wave;               /* [n_steps] or NULL: J^{n+1/2} of source 0 */
     double *fields;                 /* [6][(nz+1)(ny+1)(nx+1)] or NULL */
+    double *vsrc_current;           /* [n_steps] or NULL: I^{n+1/2} of voltage source 0 [A] */
 } oracle_outputs;
 
 /* Eq. 9: resonant frequency of the PEC/PMC cavity model of a board. */
@@ -294,8 +305,32 @@ int oracle_run(const oracle_problem *P, oracle_outputs *O)
     /* --- H neighbour fetch with the outer-wall rule for indices one past the grid --- */
 #define HGET(c, i, j, k) hget(H, c, i, j, k, nx, ny, nz, P->walls)
 
+    /* --- voltage-source edges: existing, outside the UPML, not PEC, Rs > 0 --- */
+    int bad = 0;
+    double *ve_old = calloc(P->n_vsrc > 0 ? P->n_vsrc : 1, sizeof(double));
+    double *vd_old = calloc(P->n_vsrc > 0 ? P->n_vsrc : 1, sizeof(double));
+    if (!ve_old || !vd_old) bad = -3;
+    for (int s = 0; s < P->n_vsrc && !bad; s++) {
+        const int32_t *q = P->vsrc + 4 * s;
+        const int id[3] = {q[0], q[1], q[2]}, c = q[3];
+        if (c < 0 || c > 2) { bad = -4; break; }
+        for (int w = 0; w < 3; w++) {
+            const int hi = w == c ? Nw[w] - 1 : Nw[w];
+            if (id[w] < 0 || id[w] > hi) bad = -4;
+        }
+        if (bad) break;
+        for (int w = 0; w < 3; w++) {
+            double sg, kp;
+            const int dlo = P->upml_depth[2 * w], dhi = P->upml_depth[2 * w + 1];
+            grade(id[w] + (w == c ? 0.5 : 0.0), Nw[w], dlo, dhi, 1.0, 1.0, P->upml_m, P->upml_kappa_max, &sg, &kp);
+            if (sg != 0.0 || kp != 1.0) bad = -4;
+        }
+        if (AT(pec[c], id[0], id[1], id[2])) bad = -5;
+        if (!(P->vsrc_prm[4 * s + 3] > 0.0)) bad = -6;
+    }
+
     const int Q = P->n_bins;
-    const int N = P->n_steps;
+    const int N = bad ? 0 : P->n_steps;
     for (int n = 0; n < N; n++) {
         /* ---- electric energy of E^n ---- */
         double we = 0.0, wh = 0.0;
@@ -382,6 +417,13 @@ int oracle_run(const oracle_problem *P, oracle_outputs *O)
             if (s == 0 && O->src_wave) O->src_wave[n] = js;
         }
 
+        /* E^n and D^n on the voltage-source edges (their update is redone below) */
+        for (int s = 0; s < P->n_vsrc; s++) {
+            const int32_t *q = P->vsrc + 4 * s;
+            ve_old[s] = AT(E[q[3]], q[0], q[1], q[2]);
+            vd_old[s] = AT(D[q[3]], q[0], q[1], q[2]);
+        }
+
         /* ---- D^{n+1}, E^{n+1} from H^{n+1/2} and J^{n+1/2} (Ampere with UPML) ---- */
         #pragma omp parallel for num_threads(nt) schedule(static)
         for (int k = 0; k <= nz; k++)
@@ -428,6 +470,31 @@ int oracle_run(const oracle_problem *P, oracle_outputs *O)
                     }
                 }
 
+        /* ---- resistive voltage sources: Ampere at the edge with the lumped
+         *      current I = (l E^{n+1/2} + Vs)/Rs, solved for E^{n+1} ---- */
+        for (int s = 0; s < P->n_vsrc; s++) {
+            const int32_t *q = P->vsrc + 4 * s;
+            const double *pr = P->vsrc_prm + 4 * s;
+            const int i = q[0], j = q[1], k = q[2], c = q[3];
+            double curl;
+            if (c == 0) curl = (HGET(2, i, j, k) - HGET(2, i, j - 1, k)) / dy - (HGET(1, i, j, k) - HGET(1, i, j, k - 1)) / dz;
+            else if (c == 1) curl = (HGET(0, i, j, k) - HGET(0, i, j, k - 1)) / dz - (HGET(2, i, j, k) - HGET(2, i - 1, j, k)) / dx;
+            else curl = (HGET(1, i, j, k) - HGET(1, i - 1, j, k)) / dx - (HGET(0, i, j, k) - HGET(0, i, j - 1, k)) / dy;
+            const double l = c == 0 ? dx : (c == 1 ? dy : dz);
+            const double A = V / l, R = pr[3];
+            const double eps = EPS0 * AT(epsE[c], i, j, k);
+            const double vs = oracle_pulse(pr[0], pr[1], pr[2], t_half);
+            const double rhs_j = curl - AT(J[c], i, j, k);
+            /* eps (E' - E)/dt = rhs_j - (l (E + E')/2 + vs) / (R A) */
+            const double a = dt * l / (2.0 * eps * R * A);
+            const double Eo = ve_old[s];
+            const double En = ((1.0 - a) * Eo + dt / eps * rhs_j - dt * vs / (eps * R * A)) / (1.0 + a);
+            const double I = (l * 0.5 * (Eo + En) + vs) / R;
+            AT(E[c], i, j, k) = En;
+            AT(D[c], i, j, k) = vd_old[s] + dt * (rhs_j - I / A);
+            if (s == 0 && O->vsrc_current) O->vsrc_current[n] = I;
+        }
+
         /* ---- probes and running DFT of E^{n+1} ---- */
         for (int p = 0; p < P->n_probe; p++) {
             const int32_t *q = P->probe + 4 * p;
@@ -454,6 +521,8 @@ int oracle_run(const oracle_problem *P, oracle_outputs *O)
         free(E[c]); free(H[c]); free(D[c]); free(B[c]); free(J[c]); free(epsE[c]); free(pec[c]);
         free(ci[c]); free(chf[c]);
     }
-    return 0;
+    free(ve_old);
+    free(vd_old);
+    return bad;
 #undef AT
 }

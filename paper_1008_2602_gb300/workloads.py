@@ -58,6 +58,10 @@ class Problem:
     name: str = ""
     board: Optional[Tuple[int, int, int, int]] = None   # (i0, i1, j0, j1) board cells
     dielectric_k: Optional[List[Tuple[int, int]]] = None  # per pair: (k0, k1) cell range
+    # resistive voltage sources: int32 [n, 4] (i, j, k, comp) and float64 [n, 4]
+    # (V0 [V], t0 [s], tau [s], Rs [ohm]), same pulse shape as Eq. 8
+    vsources: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4), np.int32))
+    vsource_params: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((0, 4), np.float64))
 
     @property
     def cells(self) -> int:
@@ -298,6 +302,15 @@ def add_ports(prob: Problem, sources: Sequence[Tuple[int, int, int, int]],
     return prob.replace(sources=src, source_params=prm,
                         probes=np.asarray(probes, np.int32).reshape(-1, 4),
                         n_steps=n_steps or prob.n_steps, f_max=f_max)
+
+
+def add_voltage_sources(prob: Problem, edges: Sequence[Tuple[int, int, int, int]], V0: float = 5.0,
+                        t0: float = 40 * PS, tau: float = 15 * PS, Rs: float = 10.0) -> Problem:
+    """Append resistive voltage sources (amplitude V0, series resistance Rs)."""
+    e = np.asarray(edges, np.int32).reshape(-1, 4)
+    prm = np.tile(np.array([[V0, t0, tau, Rs]], np.float64), (len(e), 1))
+    return prob.replace(vsources=np.vstack([np.asarray(prob.vsources, np.int32).reshape(-1, 4), e]),
+                        vsource_params=np.vstack([np.asarray(prob.vsource_params, np.float64).reshape(-1, 4), prm]))
 
 
 def random_problem(seed: int, nx: int, ny: int, nz: int, upml: int = 3, n_mat: int = 3,
