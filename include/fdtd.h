@@ -131,6 +131,20 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
 int fdtd_set_source(fdtd_ctx *ctx, int i, int j, int k, int comp, double J0, double t0, double tau,
                     int *src_id);
 
+/* Add a resistive voltage source on an E edge (Results section: the Table 1
+ * run drives the board with V0 = 5 V through Rs = 10 ohm, implemented with
+ * semi-implicit update coefficients; the pulse has the shape of Eq. 8,
+ * Vs(t) = V0 ((t - t0)/tau) exp(-((t - t0)/tau)^2) at t = (n + 1/2) dt).
+ * Vs in series with Rs drives the current I = (l E^{n+1/2} + Vs)/Rs through
+ * the edge (l its length, E^{n+1/2} the mean of E^n and E^{n+1}), which
+ * enters Ampere's law as curl H - I/A (A = cell volume / l); Vs is the
+ * open-circuit voltage of the edge's lower node over its upper one.
+ * Rs = +infinity leaves the edge open.  Same edge rules as fdtd_set_source
+ * (exists, outside the UPML, not PEC); only before the first step.
+ * *src_id (optional) receives the index among all sources. */
+int fdtd_set_voltage_source(fdtd_ctx *ctx, int i, int j, int k, int comp, double V0, double t0, double tau,
+                            double Rs, int *src_id);
+
 /* Add a probe on E edge (i, j, k, comp): samples E^{n+1} after every step
  * (Results section: ground-plane E_z).  Only before the first fdtd_step. */
 int fdtd_add_probe(fdtd_ctx *ctx, int i, int j, int k, int comp, int *probe_id);

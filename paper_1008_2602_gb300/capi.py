@@ -59,6 +59,8 @@ _SIGS = {
     "fdtd_create": (c_int, [P(fdtd_grid), c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, P(fdtd_boundary),
                             c_int, c_void_p, P(c_void_p)]),
     "fdtd_set_source": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double, P(c_int)]),
+    "fdtd_set_voltage_source": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
+                                        c_double, P(c_int)]),
     "fdtd_add_probe": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P(c_int)]),
     "fdtd_set_spectrum": (c_int, [c_void_p, c_double, c_int]),
     "fdtd_step": (c_int, [c_void_p, c_int]),

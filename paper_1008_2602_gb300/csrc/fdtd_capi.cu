@@ -364,12 +364,18 @@ int finalize(fdtd_ctx *c)
     if (c->started) return FDTD_OK;
     double s = 1.0;
     if (c->prec != FDTD_FP32 && !c->src.empty()) {
-        double jmax = 0.0;
-        for (const Source &S : c->src) jmax = std::max(jmax, std::fabs(S.J0));
-        if (jmax > 0.0) s = std::exp2(std::ceil(std::log2(c->dt * jmax / kEps0)));
+        // field magnitude the sources drive: dt J0 / eps0 for a current, V0 / l for a voltage
+        const double d[3] = {c->g.dx, c->g.dy, c->g.dz};
+        double emax = 0.0;
+        for (const Source &S : c->src)
+            emax = std::max(emax, S.kind == kSrcCurrent ? c->dt * std::fabs(S.J0) / kEps0 : std::fabs(S.J0) / d[S.comp]);
+        if (emax > 0.0) s = std::exp2(std::ceil(std::log2(emax)));
     }
     c->h.scale = (float)s;
-    for (Source &S : c->src) S.coef = S.coef / s;   // coef was stored as ce dt / eps0
+    for (Source &S : c->src) {   // coef was stored as ce dt / eps0, gam in V/m per V
+        S.coef = S.coef / s;
+        S.gam = S.gam / s;
+    }
     if (!c->src.empty()) {
         Source *d = nullptr;
         if (int r = dalloc(c, &d, sizeof(Source) * c->src.size())) return r;
@@ -903,6 +909,48 @@ int fdtd_set_source(fdtd_ctx *c, int i, int j, int k, int comp, double J0, doubl
     return FDTD_OK;
 }
 
+// Lumped-element factors of a resistive voltage source on an edge of length
+// l and cross-section area = V / l with permittivity eps0 / ce: Ampere's law
+// eps (E' - E)/dt = curl H - (l (E + E')/2 + Vs) / (Rs area) gives
+// E' = (E_plain - beta E - gam Vs) / (1 + beta), E_plain = E + dt curl H / eps.
+void vsource_coef(const fdtd_ctx *c, Source &S, float ce, double scale)
+{
+    const double d[3] = {c->g.dx, c->g.dy, c->g.dz};
+    const double l = d[S.comp], area = d[0] * d[1] * d[2] / l;
+    const double eps = kEps0 / (double)ce;
+    S.beta = c->dt * l / (2.0 * eps * S.rs * area);
+    S.gam = c->dt / (eps * S.rs * area) / scale;
+}
+
+int fdtd_set_voltage_source(fdtd_ctx *c, int i, int j, int k, int comp, double V0, double t0, double tau,
+                            double Rs, int *src_id)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->started) return fail(FDTD_ESTATE, "sources must be added before the first step");
+    if (!edge_exists(c, i, j, k, comp)) return fail(FDTD_EINVAL, "source edge does not exist");
+    if (!(tau > 0)) return fail(FDTD_EINVAL, "tau must be positive");
+    if (!(Rs > 0)) return fail(FDTD_EINVAL, "Rs must be positive (infinity: an open edge)");
+    Axes A;
+    build_axes(c, A);
+    const int idx[3] = {i, j, k};
+    for (int a = 0; a < 3; ++a)
+        if (!trivial(A.cw[a][a == comp ? 1 : 0][idx[a]]))
+            return fail(FDTD_EINVAL, "source edge lies inside the UPML");
+    const float4 row = c->ctab[edge_combo(c, node_index(c->h, i, j, k))];
+    const float ce = comp == 0 ? row.x : comp == 1 ? row.y : row.z;
+    if (ce == 0.0f) return fail(FDTD_EINVAL, "source edge is PEC");
+    Source S{};
+    S.node = node_index(c->h, i, j, k);
+    S.comp = comp;
+    S.kind = kSrcResistiveVoltage;
+    S.J0 = V0; S.t0 = t0; S.tau = tau;
+    S.rs = Rs;
+    vsource_coef(c, S, ce, 1.0);
+    c->src.push_back(S);
+    if (src_id) *src_id = (int)c->src.size() - 1;
+    return FDTD_OK;
+}
+
 int fdtd_add_probe(fdtd_ctx *c, int i, int j, int k, int comp, int *probe_id)
 {
     if (!c) return fail(FDTD_EINVAL, "NULL context");
@@ -1250,7 +1298,10 @@ int fdtd_set_materials(fdtd_ctx *c, const uint8_t *mat_ids)
             const float4 row = c->ctab[edge_combo(c, S.node)];
             const float ce = S.comp == 0 ? row.x : S.comp == 1 ? row.y : row.z;
             if (ce == 0.0f) return fail(FDTD_EINVAL, "a source edge became PEC");
-            S.coef = (double)ce * c->dt / kEps0 / (c->started ? c->h.scale : 1.0);
+            if (S.kind == kSrcCurrent)
+                S.coef = (double)ce * c->dt / kEps0 / (c->started ? c->h.scale : 1.0);
+            else
+                vsource_coef(c, S, ce, c->started ? c->h.scale : 1.0);
         }
         if (c->started)
             CK(cudaMemcpyAsync((void *)c->h.src, c->src.data(), sizeof(Source) * c->src.size(), cudaMemcpyHostToDevice,

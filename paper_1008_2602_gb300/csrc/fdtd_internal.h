@@ -69,12 +69,16 @@ struct Slab {
     float *aux[6];                // D~x, D~y, D~z, B~x, B~y, B~z or nullptr
 };
 
+enum SourceKind : int { kSrcCurrent = 0, kSrcResistiveVoltage = 1 };
+
 struct Source {
     long long node;               // linear node index
     int comp;                     // 0..2
-    int pad;
-    double J0, t0, tau;           // Eq. 8
-    double coef;                  // ce * dt / (eps0 s): E/s -= coef * J
+    int kind;                     // SourceKind
+    double J0, t0, tau;           // Eq. 8 pulse (amplitude J0 [A/m^2], or V0 [V] for a voltage source)
+    double coef;                  // current: ce * dt / (eps0 s), E/s -= coef * J
+    double beta, gam;             // voltage: E' = (E_plain - beta E - gam Vs) / (1 + beta) (gam includes 1/s)
+    double rs;                    // voltage: series resistance [ohm]
 };
 
 struct Probe {

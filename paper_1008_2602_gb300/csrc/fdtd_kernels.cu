@@ -973,9 +973,18 @@ __global__ void k_post(Plan plan)
         for (int s = 0; s < B->n_src; ++s) {
             const Source &S = B->src[s];
             const double u = (t - S.t0) / S.tau;
-            const double J = S.J0 * u * exp(-u * u);
+            const double w = S.J0 * u * exp(-u * u);   // Eq. 8 pulse: J, or Vs for a voltage source
             T *e = (T *)B->f[out][S.comp] + S.node;
-            Io<T>::st(e, __fsub_rn(Io<T>::ldw(e), (float)(S.coef * J)));
+            if (S.kind == kSrcCurrent) {
+                Io<T>::st(e, __fsub_rn(Io<T>::ldw(e), (float)(S.coef * w)));
+            } else {
+                // resistive voltage source: the lumped current (l E^{n+1/2} + Vs)/Rs
+                // in Ampere's law turns the plain update E_p = E^n + ce S curl into
+                // E^{n+1} = (E_p - beta E^n - gam Vs) / (1 + beta)
+                const double ep = Io<T>::ldw(e);
+                const double en = Io<T>::ldw((const T *)B->f[out ^ 1][S.comp] + S.node);
+                Io<T>::st(e, (float)((ep - S.beta * en - S.gam * w) / (1.0 + S.beta)));
+            }
         }
     }
     __syncthreads();

@@ -49,6 +49,10 @@ class Solver:
             for (i, j, k, comp), (J0, t0, tau) in zip(np.asarray(prob.sources).reshape(-1, 4),
                                                       np.asarray(prob.source_params).reshape(-1, 3)):
                 C.fdtd_set_source(ctx, int(i), int(j), int(k), int(comp), float(J0), float(t0), float(tau), None)
+            for (i, j, k, comp), (V0, t0, tau, Rs) in zip(np.asarray(prob.vsources).reshape(-1, 4),
+                                                          np.asarray(prob.vsource_params).reshape(-1, 4)):
+                C.fdtd_set_voltage_source(ctx, int(i), int(j), int(k), int(comp), float(V0), float(t0),
+                                          float(tau), float(Rs), None)
             for (i, j, k, comp) in np.asarray(prob.probes).reshape(-1, 4):
                 C.fdtd_add_probe(ctx, int(i), int(j), int(k), int(comp), None)
             if spectrum and prob.n_steps > 0 and len(prob.probes):

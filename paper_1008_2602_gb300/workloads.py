@@ -313,6 +313,22 @@ def add_voltage_sources(prob: Problem, edges: Sequence[Tuple[int, int, int, int]
                         vsource_params=np.vstack([np.asarray(prob.vsource_params, np.float64).reshape(-1, 4), prm]))
 
 
+def table1_board(n_steps: int = 30000, air=(3, 3, 3), upml=(6, 6, 6)) -> Problem:
+    """The Table 1 run of the Results section: a 40 x 30 x 0.8 mm board of
+    eps_r = 4.0 (the value that reproduces the table's predicted column; the
+    paper does not state it) between two zero-thickness PEC sheets, 2/2/0.4 mm
+    cells, dt = 1 ps, a resistive voltage source (V0 = 5 V, Rs = 10 ohm, the
+    Eq. 8 pulse shape with t0 = 100 ps, tau = 50 ps as stated for the current
+    source) on the E_z edge at one corner of the board and the E_z probe at
+    the opposite corner; air gap and UPML sizes are not given (defaults here)."""
+    p, _ = pcb_stack(board_cells=(20, 15), layers=[("pec", 0, 0), ("diel", 2, 4.0), ("pec", 0, 0)],
+                     air=air, upml=upml, d=(2 * MM, 2 * MM, 0.4 * MM), sheet_thickness=0)
+    i0, i1, j0, j1 = p.board
+    k0, _ = p.dielectric_k[0]
+    p = add_ports(p, [], [(i1 - 1, j1 - 1, k0, 2)], n_steps=n_steps).replace(dt=1e-12, name="table1_board")
+    return add_voltage_sources(p, [(i0 + 1, j0 + 1, k0, 2)], V0=5.0, t0=100 * PS, tau=50 * PS, Rs=10.0)
+
+
 def random_problem(seed: int, nx: int, ny: int, nz: int, upml: int = 3, n_mat: int = 3,
                    n_src: int = 2, n_probe: int = 4, n_steps: int = 60,
                    d=(1 * MM, 1.5 * MM, 0.5 * MM)) -> Problem:

@@ -98,21 +98,6 @@ def _table1():
     return rows
 
 
-def table1_board(n_steps=30000):
-    """The Table 1 run of the Results section: 40 x 30 x 0.8 mm board of
-    eps_r = 4.0 (reading of the unstated value) between two zero-thickness
-    PEC sheets, 2/2/0.4 mm cells, dt = 1 ps, a resistive voltage source
-    (V0 = 5 V, Rs = 10 ohm, the Eq. 8 pulse shape with t0 = 100 ps,
-    tau = 50 ps as stated for the current source) at one corner and the E_z
-    probe at the opposite one; the air gap and UPML sizes are not given."""
-    p, _ = W.pcb_stack(board_cells=(20, 15), layers=[("pec", 0, 0), ("diel", 2, 4.0), ("pec", 0, 0)],
-                       air=(3, 3, 3), upml=(6, 6, 6), d=(2e-3, 2e-3, 0.4e-3), sheet_thickness=0)
-    i0, i1, j0, j1 = p.board
-    k0, _ = p.dielectric_k[0]
-    p = W.add_ports(p, [], [(i1 - 1, j1 - 1, k0, 2)], n_steps=n_steps).replace(dt=1e-12)
-    return W.add_voltage_sources(p, [(i0 + 1, j0 + 1, k0, 2)], V0=5.0, t0=100e-12, tau=50e-12, Rs=10.0)
-
-
 def spectral_peaks(x, dt, f_top=10.5e9):
     pad = 4
     X = np.abs(np.fft.rfft(x * np.hanning(len(x)), pad * len(x)))
@@ -126,7 +111,7 @@ def test_table1_run_with_the_resistive_source(ncpu):
     nearest oracle peak of each of the five lowest isolated modes must sit in
     that band widened by 1 % on each side, and no peak may lie below the
     fundamental."""
-    p = table1_board()
+    p = W.table1_board()
     r = oracle.run(p, dft=False, n_threads=ncpu)
     peaks = spectral_peaks(r["trace"][0], r["dt"])
     rows = {(m, n): pred * 1e9 for m, n, pred, _, _ in _table1()}

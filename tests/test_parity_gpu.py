@@ -324,3 +324,28 @@ def test_checkpoint_resume_is_bitwise(fdtd):
     assert other.info()["step"] == 0
     for s in (ref, b, other):
         s.close()
+
+
+def test_resistive_voltage_source_matches_oracle(fdtd, ncpu):
+    """A resistive voltage source (V0, Rs in series on an E edge) next to a
+    current source on a random-material grid: traces and fields against the
+    oracle's semi-implicit lumped-element update; the open (Rs = inf) source
+    leaves the run unchanged bit for bit."""
+    p = W.random_problem(17, 30, 24, 18, upml=3, n_steps=400)
+    s0 = p.sources[0]
+    q = W.add_voltage_sources(p, [(int(s0[0]) + 2, int(s0[1]) + 1, int(s0[2]), 2)], V0=5.0, Rs=10.0)
+    ref = oracle.run(q, n_threads=ncpu, fields=True, dft=False)
+    s = fdtd.Solver(q)
+    s.run()
+    tr = s.traces()
+    for k in range(len(tr)):
+        assert rel_l2(tr[k], ref["trace"][k]) <= 1e-4, k
+    _fields_close(s, ref["fields"])
+    s.close()
+    a = fdtd.Solver(p)
+    a.run()
+    b = fdtd.Solver(W.add_voltage_sources(p, [(int(s0[0]) + 2, int(s0[1]) + 1, int(s0[2]), 2)], Rs=np.inf))
+    b.run()
+    assert np.array_equal(a.traces(), b.traces())
+    a.close()
+    b.close()
