@@ -184,6 +184,12 @@ int fdtd_probe_trace(fdtd_ctx *ctx, int probe, float *out, int max_len, int *len
  * H is H^{n-1/2} after n steps.  Synchronises. */
 int fdtd_get_field(fdtd_ctx *ctx, int field, float *out);
 
+/* Copy one node plane k (0 <= k <= nz) of a field component to host
+ * out[(ny+1)(nx+1)] as FP32 in SI units, layout [j][i], with the conventions
+ * of fdtd_get_field: headless snapshots, e.g. of the ground-plane E_z of the
+ * Results section's Figs. 3-4.  Synchronises. */
+int fdtd_get_plane(fdtd_ctx *ctx, int field, int k, float *out);
+
 /* Discrete energy W = 1/2 V (sum eps E^{n-1}.E^{n-1} + sum mu0 H^{n-3/2}.H^{n-1/2})
  * of the last completed step (exactly conserved by the Yee scheme in a
  * lossless closed box) and max |div B| [T/m] over cells outside the UPML,

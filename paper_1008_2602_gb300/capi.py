@@ -62,6 +62,7 @@ _SIGS = {
     "fdtd_set_voltage_source": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_double, c_double, c_double,
                                         c_double, P(c_int)]),
     "fdtd_add_probe": (c_int, [c_void_p, c_int, c_int, c_int, c_int, P(c_int)]),
+    "fdtd_get_plane": (c_int, [c_void_p, c_int, c_int, c_void_p]),
     "fdtd_set_spectrum": (c_int, [c_void_p, c_double, c_int]),
     "fdtd_step": (c_int, [c_void_p, c_int]),
     "fdtd_step_profiled": (c_int, [c_void_p, c_int, P(c_double)]),

@@ -1119,6 +1119,30 @@ int fdtd_get_field(fdtd_ctx *c, int field, float *out)
     return FDTD_OK;
 }
 
+int fdtd_get_plane(fdtd_ctx *c, int field, int k, float *out)
+{
+    if (!c || !out) return fail(FDTD_EINVAL, "NULL argument");
+    if (field < 0 || field > 5) return fail(FDTD_EINVAL, "field must be 0..5");
+    if (k < 0 || k > c->h.nz) return fail(FDTD_EINVAL, "plane index out of range");
+    if (int r = fdtd_sync(c)) return r;
+    const Board &h = c->h;
+    const int par = (int)(c->host_step & 1);
+    const int es = elem_size(c->prec);
+    const int NX = h.nx + 1, NY = h.ny + 1;
+    std::vector<unsigned char> buf((size_t)NX * NY * es);
+    const unsigned char *src = static_cast<const unsigned char *>(h.f[par][field]) + (size_t)k * h.plane * es;
+    CK(cudaMemcpy2D(buf.data(), (size_t)NX * es, src, (size_t)h.pitch * es, (size_t)NX * es, NY, cudaMemcpyDeviceToHost));
+    const double s = field < 3 ? h.scale : h.scale / kEta0;
+    for (size_t t = 0; t < (size_t)NX * NY; ++t) {
+        float v;
+        if (c->prec == FDTD_FP32) v = ((const float *)buf.data())[t];
+        else if (c->prec == FDTD_FP16_STORE) v = __half2float(((const __half *)buf.data())[t]);
+        else v = __bfloat162float(((const __nv_bfloat16 *)buf.data())[t]);
+        out[t] = (float)(v * s);
+    }
+    return FDTD_OK;
+}
+
 int fdtd_diagnostics(fdtd_ctx *c, double *energy, double *max_div_b)
 {
     if (!c) return fail(FDTD_EINVAL, "NULL context");

@@ -147,6 +147,13 @@ class Solver:
         C.fdtd_get_field(self.ctx, int(comp), out.ctypes.data)
         return out
 
+    def plane(self, comp: int, k: int) -> np.ndarray:
+        """Node plane k of one component, [ny+1, nx+1] FP32 in SI units (fdtd_get_plane)."""
+        p = self.problem
+        out = np.zeros((p.ny + 1, p.nx + 1), dtype=np.float32)
+        C.fdtd_get_plane(self.ctx, int(comp), int(k), out.ctypes.data)
+        return out
+
     def diagnostics(self):
         e, d = ctypes.c_double(), ctypes.c_double()
         C.fdtd_diagnostics(self.ctx, ctypes.byref(e), ctypes.byref(d))

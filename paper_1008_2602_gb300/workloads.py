@@ -329,6 +329,20 @@ def table1_board(n_steps: int = 30000, air=(3, 3, 3), upml=(6, 6, 6)) -> Problem
     return add_voltage_sources(p, [(i0 + 1, j0 + 1, k0, 2)], V0=5.0, t0=100 * PS, tau=50 * PS, Rs=10.0)
 
 
+def fig3_board(n_steps: int = 1000, eps_r: float = 4.0, air=(3, 3, 3), upml=(8, 8, 6)) -> Problem:
+    """The board of the Results section's Figs. 3-4: 100 x 60 x 0.8 mm, 2/2/0.4
+    mm cells, dt = 1 ps, current source (Eq. 8, J0 = 1 A/mm^2, t0 = 100 ps,
+    tau = 50 ps) on the E_z edge at the centre of the board, UPML around it.
+    eps_r, the air gap and the UPML depth are not given (defaults here; eps_r
+    as read for Table 1).  The grid is mirror-symmetric about the source."""
+    p, _ = pcb_stack(board_cells=(50, 30), layers=[("pec", 0, 0), ("diel", 2, eps_r), ("pec", 0, 0)],
+                     air=air, upml=upml, d=(2 * MM, 2 * MM, 0.4 * MM), sheet_thickness=0)
+    k0, _ = p.dielectric_k[0]
+    ic, jc = p.nx // 2, p.ny // 2
+    return add_ports(p, [(ic, jc, k0, 2)], [(ic, jc, k0, 2)], J0=1e6, t0=100 * PS, tau=50 * PS,
+                     n_steps=n_steps).replace(dt=1e-12, name="fig3_board")
+
+
 def random_problem(seed: int, nx: int, ny: int, nz: int, upml: int = 3, n_mat: int = 3,
                    n_src: int = 2, n_probe: int = 4, n_steps: int = 60,
                    d=(1 * MM, 1.5 * MM, 0.5 * MM)) -> Problem:
