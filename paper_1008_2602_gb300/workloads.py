@@ -343,6 +343,30 @@ def fig3_board(n_steps: int = 1000, eps_r: float = 4.0, air=(3, 3, 3), upml=(8, 
                      n_steps=n_steps).replace(dt=1e-12, name="fig3_board")
 
 
+def zrefine_board(nz_d: int, dt: float, n_steps: int, eps_r: float = 4.0, board_cells=(20, 15),
+                  air_xy: int = 3, upml_xy: int = 6, air_z_mm: float = 2.4, upml_z_mm: float = 4.8) -> Problem:
+    """The z-convergence model of the Results section: a 40 x 30 mm plane pair
+    with a 0.8 mm dielectric cut into nz_d cells (2 mm cells in x and y); the
+    air above and below and the z UPML keep their thickness in mm (rounded to
+    whole cells), so only the board's z discretisation changes.
+    The current source is a filament across the whole gap (every E_z edge of
+    the dielectric at one corner carries J0 = 1 A/mm^2 with the Eq. 8 pulse,
+    t0 = 100 ps, tau = 50 ps), so its total current does not depend on the
+    cutting; the probes are every E_z edge of the column at the opposite corner,
+    whose sum times dz is the voltage between the planes."""
+    dz = 0.8 * MM / nz_d
+    az, uz = int(round(air_z_mm * MM / dz)), int(round(upml_z_mm * MM / dz))
+    p, _ = pcb_stack(board_cells=board_cells, layers=[("pec", 0, 0), ("diel", nz_d, eps_r), ("pec", 0, 0)],
+                     air=(air_xy, air_xy, az), upml=(upml_xy, upml_xy, uz), d=(2 * MM, 2 * MM, dz),
+                     sheet_thickness=0)
+    i0, i1, j0, j1 = p.board
+    k0, k1 = p.dielectric_k[0]
+    src = [(i0 + 1, j0 + 1, k, 2) for k in range(k0, k1)]
+    prb = [(i1 - 1, j1 - 1, k, 2) for k in range(k0, k1)]
+    return add_ports(p, src, prb, J0=1e6, t0=100 * PS, tau=50 * PS, n_steps=n_steps).replace(
+        dt=dt, name=f"zrefine_{nz_d}")
+
+
 def random_problem(seed: int, nx: int, ny: int, nz: int, upml: int = 3, n_mat: int = 3,
                    n_src: int = 2, n_probe: int = 4, n_steps: int = 60,
                    d=(1 * MM, 1.5 * MM, 0.5 * MM)) -> Problem:
