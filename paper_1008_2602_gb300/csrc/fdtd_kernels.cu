@@ -1,28 +1,30 @@
 // fdtd_kernels.cu -- sm_103a kernels of the Yee + UPML leapfrog step.
 //
 // One step (Model section: H at half steps from E, then E from H and J) is
-// four launches over a Plan (one board or a batch of boards):
-//   k_slab_h     H^{n+1/2} (and B~) on UPML/boundary slab nodes   (Eqs. 1-5)
-//   k_interior   fused H^{n+1/2} and E^{n+1} on the interior box (plain Yee,
-//                uint8 coefficient ids; halo H recomputed or read from slabs)
-//   k_slab_e     E^{n+1} (and D~) on slab nodes, PEC/PMC outer walls
-//   k_post       current sources (Eq. 8) and probe samples of E^{n+1}
+// five launches over a Plan (one board or a batch of boards):
+//   k_slab_h        H^{n+1/2} (and B~) on the x/y UPML slabs and the two
+//                   outer z planes                                  (Eqs. 1-5)
+//   k_fused<..,1>   fused H^{n+1/2} and E^{n+1} on the interior columns'
+//                   z-UPML planes (sigma_z only; B~z, D~z staged by TMA)
+//   k_fused<..,0>   fused H^{n+1/2} and E^{n+1} on the interior columns'
+//                   remaining planes (plain Yee, coefficient ids, TMA-fed)
+//   k_slab_e        E^{n+1} (and D~) on the slab nodes, PEC/PMC outer walls
+//   k_post          current sources (Eq. 8), resistive voltage sources
+//                   (Results section) and probe samples of E^{n+1}
 // and, once per chunk, k_dft folds the new probe samples into the FP64
 // running DFT (Results section: spectrum of the ground-plane E_z) with warp
 // shuffles.  Fields are ping-ponged, so no launch reads what it writes except
 // the per-node UPML auxiliaries, which only their own thread touches.
 //
-// All curl and update arithmetic goes through curl2()/the update helpers with
-// explicit round-to-nearest intrinsics, so a value recomputed as a halo is
-// bit-identical to the one its owner stores.
+// All curl and update arithmetic goes through curl2()/the update helpers (or
+// their paired FFMA2 forms) with explicit round-to-nearest intrinsics, so a
+// value recomputed as a halo is bit-identical to the one its owner stores.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "fdtd_internal.h"
 
 namespace fdtd {
-
-
 
 // ------------------------------------------------------------------ storage
 template <typename T>
