@@ -5,6 +5,7 @@
 // uint8 id per node, Eq. 5 grading -> 1D UPML factors per axis, Eq. 7 time
 // step, slab decomposition of the UPML), owns device memory, captures chunks
 // of steps into CUDA graphs and batches boards into one launch per phase.
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -564,12 +565,19 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     return FDTD_OK;
 }
 
+// NVTX range over a host-side call, for profiler timelines (no cost without a tool attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
 // Run n steps of `plan` on stream st: CUDA graphs of `chunk` steps (each
 // ending with the running-DFT update), direct launches for the remainder.
 int run_steps(const Plan &plan, int prec, int grid_cap, int n, int chunk, cudaGraphExec_t &graph, int &graph_chunk,
               cudaStream_t st)
 {
     if (n <= 0) return FDTD_OK;
+    NvtxRange range(plan.nb > 1 ? "fdtd batch steps" : "fdtd steps");
     if (chunk > 1 && n >= chunk) {
         if (!graph || graph_chunk != chunk) {
             if (graph) cudaGraphExecDestroy(graph);
