@@ -349,3 +349,48 @@ def test_resistive_voltage_source_matches_oracle(fdtd, ncpu):
     assert np.array_equal(a.traces(), b.traces())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("shape,upml,src", [
+    ((1, 1, 1), (0,) * 6, (0, 0, 0, 2)),               # one cell: no fused region, every node a slab node
+    ((6, 5, 1), (0,) * 6, (3, 2, 0, 2)),               # a single z cell (one-plane z-march slabs)
+    ((1, 7, 6), (0,) * 6, (0, 3, 2, 2)),               # a single x cell
+    ((12, 10, 8), (4,) * 6, (5, 5, 4, 0)),             # UPML on every face leaves no interior columns
+    ((14, 12, 9), (6, 6, 6, 6, 4, 4), (7, 6, 4, 2)),   # UPML layers meeting in the middle of y
+])
+def test_degenerate_grids_match_oracle(fdtd, ncpu, shape, upml, src):
+    """Grids at the edges of the decomposition: fields and traces against the
+    oracle element by element (the source sits on an edge outside the UPML).
+    Errors are measured against each field's natural scale, max |E| for E and
+    max(|H|, |E|/eta0) for H (the kernels hold E and eta0 H at one scale): on
+    these tiny grids a single H component can be a near-cancellation far below
+    that scale."""
+    nx, ny, nz = shape
+    walls = (PMC, PMC, PMC, PMC, PEC, PEC) if not any(upml) else (PEC,) * 6
+    p = W.box(nx, ny, nz, d=(1e-3, 1.1e-3, 0.6e-3), eps_r=2.0, walls=walls, upml=upml)
+    p = W.add_ports(p, [src], [src], n_steps=80)
+    ref = oracle.run(p, n_threads=ncpu, fields=True, dft=False)
+    s = fdtd.Solver(p)
+    s.run()
+    assert np.abs(ref["trace"]).max() > 0
+    assert rel_l2(s.traces(), ref["trace"]) <= 1e-4
+    eta0 = 4e-7 * np.pi * 299792458.0
+    me = max(np.abs(ref["fields"][c]).max() for c in range(3))
+    mh = max(max(np.abs(ref["fields"][c]).max() for c in range(3, 6)), me / eta0)
+    for c in range(6):
+        g, r = s.field(c).astype(np.float64), ref["fields"][c]
+        assert np.abs(g - r).max() <= 1e-4 * (me if c < 3 else mh), c
+    s.close()
+
+
+def test_no_sources_no_probes(fdtd):
+    """A board with neither sources nor probes steps, stays at zero and
+    reports empty spectra."""
+    p = W.random_problem(41, 20, 16, 12, upml=3, n_steps=30).replace(
+        sources=np.zeros((0, 4), np.int32), source_params=np.zeros((0, 3)), probes=np.zeros((0, 4), np.int32))
+    s = fdtd.Solver(p)
+    s.run()
+    assert s.info()["step"] == 30
+    for c in range(6):
+        assert not np.any(s.field(c))
+    s.close()
