@@ -94,7 +94,7 @@ struct fdtd_ctx {
     long long host_step = 0;
     fdtd_batch *batch = nullptr;
     // single-board plan and graph
-    fdtd_tuning tune{62, 4, 10, 16};
+    fdtd_tuning tune{62, 8, 10, 16};
     bool plan_dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;   // device [0]=board ptr, then prefixes
@@ -115,7 +115,7 @@ struct fdtd_batch {
     bool own_stream = false;
     std::vector<fdtd_ctx *> members;
     std::vector<long long> remaining;
-    fdtd_tuning tune{62, 4, 10, 16};
+    fdtd_tuning tune{62, 8, 10, 16};
     bool tuned = false;             // set_tuning called: keep the caller's tile
     bool dirty = true;
     Plan plan{};
@@ -729,8 +729,9 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     if (n_pec > 0) c->boxes.assign(pec, pec + n_pec);
     if (pec_mask) c->mask.assign(pec_mask, pec_mask + (size_t)grid->nx * grid->ny * grid->nz);
     c->prec = precision;
-    // default fused tile: 16-bit stages are half as large, so two compute
-    // warps per block (124 columns) fit as many blocks per SM as one does in FP32
+    // default fused tile: 62x8 (two compute warps of four rows sharing a
+    // stage); 16-bit stages are half as large, so 124x8 (four compute warps)
+    // fits as many blocks per SM
     if (precision != FDTD_FP32) c->tune.tile_x = 124;
     c->dt = grid->dt > 0 ? grid->dt
                          : grid->courant / (kC0 * std::sqrt(1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dy * grid->dy) +

@@ -300,7 +300,9 @@ __device__ __forceinline__ float2 curl2v(float2 a1, float2 a0, float2 b1, float2
 }
 
 // Columns owned by one compute warp: lane l holds the pair g + 2l, g + 2l + 1
-// with g the even column at or just below the strip's low-x halo.
+// with g the even column at or just below the strip's low-x halo.  A tile of
+// TY rows may be split into R row groups, one compute warp each, sharing the
+// tile's stage (each group recomputes H~ on the row above it).
 constexpr int kWarpCols = 62;
 
 // Shared-memory stage of one plane for a tile of W warps x 62 columns by TY
@@ -332,7 +334,7 @@ struct Stage {
     static constexpr int BYTES = A_OFF + (ZP ? (B_CS + D_CS) * 4 : 0);
 };
 
-template <typename T, int TY, int W, int NS, bool ZP>
+template <typename T, int TY, int W, int NS, bool ZP, int R>
 struct FusedLayout {
     using St = Stage<T, TY, W, ZP>;
     static constexpr int BAR_OFF = NS * St::BYTES;
@@ -341,7 +343,7 @@ struct FusedLayout {
     // reserved per block); the register budget keeps them resident but never drops
     // below 128 registers per thread (176 for 8-row tiles)
     static constexpr int PER_SM = 232448 / (BYTES + 1024);
-    static constexpr int REG_SM = 65536 / ((TY >= 8 ? 176 : 128) * (32 * W + 32));
+    static constexpr int REG_SM = 65536 / ((TY / R >= 8 ? 176 : (ZP ? 168 : 128)) * (32 * W * R + 32));
     static constexpr int CAP = PER_SM < REG_SM ? PER_SM : REG_SM;
     static constexpr int MINB = CAP < 1 ? 1 : (CAP > 8 ? 8 : CAP);
 };
@@ -407,7 +409,8 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 // H~^{n-1/2} with the low halo row and column, coefficient ids, and in the
 // z-UPML kernel the B~z/D~z auxiliaries of z-UPML planes), each stage with a
 // "full" mbarrier (TMA bytes) and an "empty" one (one arrival per compute
-// warp).  Compute warp w owns 62 columns [i0 + 62w, i0 + 62w + 62); lane l
+// warp).  Compute warp (w, row group) owns 62 columns [i0 + 62w, i0 + 62w + 62)
+// of its rows; lane l
 // holds the column pair (g + 2l, g + 2l + 1), g = (i0 + 62w - 1) & ~1, so
 // one lane's loads and stores are 8 bytes and its arithmetic is paired FP32
 // (FFMA2/FMUL2).  Per plane k a lane marches the tile's rows in y: it forms
@@ -420,11 +423,13 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 // only.  In z-UPML planes (sigma_z only) H~z carries B~z and E_z carries
 // D~z, while H~x, H~y, E_x, E_y update in the lossy form; those planes use
 // the scalar update helpers per element, every other plane the paired form.
-template <typename T, int TY, int W, int NS, bool ZP>
-__global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::MINB)) k_fused(Plan plan)
+template <typename T, int TY, int W, int NS, bool ZP, int R>
+__global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP, R>::MINB)) k_fused(Plan plan)
 {
     using St = Stage<T, TY, W, ZP>;
-    using L = FusedLayout<T, TY, W, NS, ZP>;
+    using L = FusedLayout<T, TY, W, NS, ZP, R>;
+    constexpr int TYW = TY / R;   // rows of one compute warp
+    static_assert(TY % R == 0, "row groups must split the tile evenly");
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
     uint64_t *empty = full + NS;
@@ -434,14 +439,14 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
     if (wy == 0 && lx == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], W);
+            mbar_init(&empty[s], W * R);
         }
         *abort_flag = 0;
         fence_mbar_init();
     }
     __syncthreads();
 
-    if (wy == W) {
+    if (wy == W * R) {
         // ------------------------------------------------------------ producer
         // Items are taken from a global counter; the first plane of an item
         // carries the item id to the compute warps, an id of -1 ends the work.
@@ -530,7 +535,9 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
         const int id16 = B->id16;
         const float4 *__restrict__ ctab = B->ctab;
         int *const status = B->status;
-        const int wlo = i0 + kWarpCols * wy;               // first column the warp owns
+        const int wx = wy % W, R0 = (wy / W) * TYW;        // column strip; first tile row of the warp
+        const int jb = j0 + R0;                            // first grid row the warp owns
+        const int wlo = i0 + kWarpCols * wx;               // first column the warp owns
         const int whi = min(wlo + kWarpCols, ix1);
         const int g = (wlo - 1) & ~1;
         const int ca = g + 2 * lx, cb = ca + 1;            // this lane's columns
@@ -539,22 +546,22 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
         const int ecol = (g - ((i0 - 1) & ~7)) + 2 * lx;   // column of ca in the E/H boxes (even)
         const int xc0 = id16 ? (i0 & ~7) : (i0 & ~15);
         const int ida = max(ca - xc0, 0), idb = cb - xc0;  // columns in the id box (clamped into it)
-        const bool row_slab = (j0 - 1 < iy0);
-        // element (ca, j0-1, kstart) of component 0 in the output parity, advanced by P per plane
-        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(j0 - 1) * X + ca);
+        const bool row_slab = (jb - 1 < iy0);
+        // element (ca, jb-1, kstart) of component 0 in the output parity, advanced by P per plane
+        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(jb - 1) * X + ca);
         const int zrow = B->zpitch;
         const long long zplane = (long long)(iy1 - iy0) * zrow;
-        const long long zcol = (long long)(j0 - iy0) * zrow + (ca - ix0);   // aux index of (ca, j0) in a plane
+        const long long zcol = (long long)(jb - iy0) * zrow + (ca - ix0);   // aux index of (ca, jb) in a plane
         const int acol = (ca - ix0) - ((((i0 - 1) & ~1) - ix0) & ~3);       // column of ca in the aux boxes
         int s0 = sq, s1 = sq + 1 == NS ? 0 : sq + 1;
 
-        float2 hk1x[TY], hk1y[TY];   // H~x, H~y of the previous plane, per row
+        float2 hk1x[TYW], hk1y[TYW];   // H~x, H~y of the previous plane, per row
 #pragma unroll
-        for (int r = 0; r < TY; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
+        for (int r = 0; r < TYW; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
         if (kstart == kb) {         // plane kb-1 is not recomputed: read its H~
 #pragma unroll
-            for (int r = 0; r < TY; ++r)
-                if (j0 + r < iy1) {
+            for (int r = 0; r < TYW; ++r)
+                if (jb + r < iy1) {
                     const T *gq = gp - P + (long long)(r + 1) * X;
                     if (own_a) { hk1x[r].x = Io<T>::ld(gq + 3 * NN); hk1y[r].x = Io<T>::ld(gq + 4 * NN); }
                     if (own_b) { hk1x[r].y = Io<T>::ld(gq + 3 * NN + 1); hk1y[r].y = Io<T>::ld(gq + 4 * NN + 1); }
@@ -565,11 +572,12 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
             mbar_wait(&full[s1], (fph >> s1) & 1u, status, abort_flag);
             fph ^= 1u << s1;
             const unsigned char *st0 = smem + s0 * St::BYTES, *st1 = smem + s1 * St::BYTES;
-            const T *E0 = reinterpret_cast<const T *>(st0 + St::E_OFF) + ecol;
-            const T *E1 = reinterpret_cast<const T *>(st1 + St::E_OFF) + ecol;
-            const T *H0 = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol;
-            const unsigned char *C0 = st0 + St::C_OFF;
-            const float *A0 = reinterpret_cast<const float *>(st0 + St::A_OFF) + acol;
+            // the warp's rows: box rows from R0 on (E, H and B~ boxes start one row above the tile)
+            const T *E0 = reinterpret_cast<const T *>(st0 + St::E_OFF) + ecol + R0 * St::EW;
+            const T *E1 = reinterpret_cast<const T *>(st1 + St::E_OFF) + ecol + R0 * St::EW;
+            const T *H0 = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol + R0 * St::HW;
+            const unsigned char *C0 = st0 + St::C_OFF + R0 * (id16 ? 2 * St::C16W : St::C8W);
+            const float *A0 = reinterpret_cast<const float *>(st0 + St::A_OFF) + acol + R0 * St::AW;
             constexpr int EW = St::EW, HW = St::HW, ECS = St::E_CS, HCS = St::H_CS;
             constexpr int AW = St::AW, BCS = St::B_CS;
             const int zb = ZP ? (k < iz0 ? 1 : (k >= iz1 ? 2 : 0)) : 0;
@@ -586,9 +594,9 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
             const bool full_plane = k >= kb;
             // coefficient rows of the lane's two nodes (ids clamped into the box,
             // so every lookup is a valid row)
-            float4 cea[TY], ceb[TY];
+            float4 cea[TYW], ceb[TYW];
 #pragma unroll
-            for (int r = 0; r < TY; ++r) {
+            for (int r = 0; r < TYW; ++r) {
                 const int ia = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + ida]
                                     : (int)C0[r * St::C8W + ida];
                 const int ib = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * St::C16W + idb]
@@ -630,7 +638,7 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
             };
             // halo elements outside the fused region come from the slab output
             auto slab_fix = [&](int rr, float2 &hx, float2 &hy, float2 &hz) {
-                if (j0 - 1 + rr >= iy1) return;
+                if (jb - 1 + rr >= iy1) return;
                 const T *gq = gp + (long long)rr * X;
                 if (slab_a) { hx.x = Io<T>::ld(gq + 3 * NN); hy.x = Io<T>::ld(gq + 4 * NN); hz.x = Io<T>::ld(gq + 5 * NN); }
                 if (slab_b) {
@@ -640,7 +648,7 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
 
             float2 px = make_float2(0.f, 0.f), pz = px;   // H~x, H~z at (., j-1)
             if (full_plane) {
-                if (row_slab) {   // row j0-1 lies in the low-y slab: read its H~ (own columns)
+                if (row_slab) {   // row jb-1 lies in the low-y slab: read its H~ (own columns)
                     if (own_a && own_b) {
                         px = Pair<T>::ldg(gp + 3 * NN);
                         pz = Pair<T>::ldg(gp + 5 * NN);
@@ -658,8 +666,8 @@ __global__ void __launch_bounds__(32 * W + 32, (FusedLayout<T, TY, W, NS, ZP>::M
                 }
             }
 #pragma unroll
-            for (int r = 0; r < TY; ++r) {
-                const int j = j0 + r, rr = r + 1;
+            for (int r = 0; r < TYW; ++r) {
+                const int j = jb + r, rr = r + 1;
                 float2 ex, ey, ez, hx, hy, hz, nbz = make_float2(0.f, 0.f);
                 hrow(rr, j < iy1, ex, ey, ez, hx, hy, hz, nbz);
                 slab_fix(rr, hx, hy, hz);
@@ -1181,11 +1189,11 @@ cudaError_t launch_wait_selftest(int *status, unsigned max_polls, cudaStream_t s
 // NS-stage ring; ZP selects the z-UPML launch.
 constexpr int kFusedStages = 3;
 
-template <typename T, int TY, int W, bool ZP>
+template <typename T, int TY, int W, bool ZP, int R>
 struct FusedCfg {
     static constexpr int NS = kFusedStages;
-    using L = FusedLayout<T, TY, W, NS, ZP>;
-    static dim3 block() { return dim3(32, W + 1); }
+    using L = FusedLayout<T, TY, W, NS, ZP, R>;
+    static dim3 block() { return dim3(32, W * R + 1); }
     static int grid()
     {
         static int g = 0;
@@ -1193,34 +1201,38 @@ struct FusedCfg {
             int dev = 0, sms = 0, per = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS, ZP>, 32 * (W + 1), L::BYTES);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS, ZP, R>, 32 * (W * R + 1),
+                                                          L::BYTES);
             g = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
         }
         return g;
     }
     static cudaError_t set_limit()
     {
-        return cudaFuncSetAttribute(k_fused<T, TY, W, NS, ZP>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+        return cudaFuncSetAttribute(k_fused<T, TY, W, NS, ZP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    L::BYTES);
     }
     static void launch(const Plan &plan, cudaStream_t st)
     {
         const long long n = ZP ? plan.n_zp : plan.n_int;
         if (n <= 0) return;
         const int g = (int)(n < grid() ? n : grid());
-        k_fused<T, TY, W, NS, ZP><<<g, block(), L::BYTES, st>>>(plan);
+        k_fused<T, TY, W, NS, ZP, R><<<g, block(), L::BYTES, st>>>(plan);
     }
 };
 
-// Supported fused tiles (tile_x columns x tile_y rows): 62x4, 62x8, 124x4, 124x8.
+// Supported fused tiles (tile_x columns x tile_y rows): 62x4 and 124x4 (one
+// compute warp per 62 columns), 62x8 and 124x8 (two compute warps of four
+// rows per 62 columns, sharing the stage).
 template <typename T, bool ZP>
 static void launch_fused(const Plan &plan, cudaStream_t st)
 {
     const int key = plan.tile_x * 16 + plan.tile_y;
     switch (key) {
-    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP>::launch(plan, st); break;
-    case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP>::launch(plan, st); break;
-    case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP>::launch(plan, st); break;
-    default: FusedCfg<T, 4, 1, ZP>::launch(plan, st); break;
+    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP, 2>::launch(plan, st); break;
+    case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP, 1>::launch(plan, st); break;
+    case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP, 2>::launch(plan, st); break;
+    default: FusedCfg<T, 4, 1, ZP, 1>::launch(plan, st); break;
     }
 }
 
@@ -1281,10 +1293,10 @@ bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (t
 template <typename T>
 static cudaError_t limits_t()
 {
-    cudaError_t e[8] = {FusedCfg<T, 4, 1, false>::set_limit(), FusedCfg<T, 8, 1, false>::set_limit(),
-                        FusedCfg<T, 4, 2, false>::set_limit(), FusedCfg<T, 8, 2, false>::set_limit(),
-                        FusedCfg<T, 4, 1, true>::set_limit(),  FusedCfg<T, 8, 1, true>::set_limit(),
-                        FusedCfg<T, 4, 2, true>::set_limit(),  FusedCfg<T, 8, 2, true>::set_limit()};
+    cudaError_t e[8] = {FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 2>::set_limit(),
+                        FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),
+                        FusedCfg<T, 4, 1, true, 1>::set_limit(),  FusedCfg<T, 8, 1, true, 2>::set_limit(),
+                        FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit()};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;

@@ -1,5 +1,5 @@
 """Parity at the benchmarked sizes, in the launch configuration bench.py times
-(default tuning: 62x4 fused tiles, 10-plane z-segments, CUDA graphs of 16
+(default tuning: 62x8 fused tiles, 10-plane z-segments, CUDA graphs of 16
 steps), against the FP64 oracle:
 
 * the full 880x680x100 multilayer board (60.6 M nodes) for 60 steps, with the
