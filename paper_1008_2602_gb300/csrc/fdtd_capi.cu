@@ -385,6 +385,12 @@ int finalize(fdtd_ctx *c)
         c->h.src = d;
     }
     c->h.n_src = (int)c->src.size();
+    {
+        std::vector<std::pair<long long, int>> edges;
+        for (const Source &S : c->src) edges.push_back({S.node, S.comp});
+        std::sort(edges.begin(), edges.end());
+        c->h.src_distinct = std::adjacent_find(edges.begin(), edges.end()) == edges.end() ? 1 : 0;
+    }
     if (!c->probe.empty()) {
         Probe *d = nullptr;
         if (int r = dalloc(c, &d, sizeof(Probe) * c->probe.size())) return r;

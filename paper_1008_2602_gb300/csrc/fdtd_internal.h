@@ -122,6 +122,8 @@ struct Board {
     long long *stop;              // inactive once *step >= *stop
     int n_src;
     int n_probe;
+    int src_distinct;             // no two sources share an edge
+    int pad3;
     const Source *src;
     const Probe *probe;
     double dt;

@@ -978,9 +978,12 @@ __global__ void k_post(Plan plan)
     if (!board_active(B)) return;
     const long long step = *((volatile long long *)B->step);
     const int out = (int)(step & 1) ^ 1;
-    if (threadIdx.x == 0) {
+    // sources on distinct edges are independent: one thread each; sources
+    // sharing an edge are applied in order by thread 0
+    const bool par_src = B->src_distinct != 0;
+    if (par_src || threadIdx.x == 0) {
         const double t = ((double)step + 0.5) * B->dt;
-        for (int s = 0; s < B->n_src; ++s) {
+        for (int s = par_src ? (int)threadIdx.x : 0; s < B->n_src; s += par_src ? (int)blockDim.x : 1) {
             const Source &S = B->src[s];
             const double u = (t - S.t0) / S.tau;
             const double w = S.J0 * u * exp(-u * u);   // Eq. 8 pulse: J, or Vs for a voltage source
