@@ -815,13 +815,28 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         h.iz0 = 1; h.iz1 = nz;
         boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
     } else {
-        boxes.push_back({0, nx + 1, 0, ny + 1, 0, 1});
-        boxes.push_back({0, nx + 1, 0, ny + 1, nz, nz + 1});
-        boxes.push_back({0, nx + 1, 0, h.iy0, 1, nz});
-        boxes.push_back({0, nx + 1, h.iy1, ny + 1, 1, nz});
-        boxes.push_back({0, h.ix0, h.iy0, h.iy1, 1, nz});
-        boxes.push_back({h.ix1, nx + 1, h.iy0, h.iy1, 1, nz});
+        // The slabs are split where the set of graded axes changes, so that each
+        // box carries only the auxiliaries its own nodes need: faces graded
+        // along one axis keep two, edges and corners six.  Per axis the node
+        // ranges are low UPML, middle and high UPML; the z ranges of the
+        // outer boxes include the wall planes k = 0 and k = nz.
+        const int xs[4] = {0, h.ix0, h.ix1, nx + 1}, ys[4] = {0, h.iy0, h.iy1, ny + 1};
+        const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), nz + 1};
+        for (int zb = 0; zb < 3; zb += 2) {
+            // z-UPML layers with the wall plane: y strips over all x, then x strips
+            for (int yb = 0; yb < 3; yb += 2) boxes.push_back({0, nx + 1, ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
+            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
+            // the wall plane of the interior columns (the fused kernels start at k = 1)
+            const int kw = zb == 0 ? 0 : nz;
+            boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
+        }
+        // planes between the z-UPML layers: y faces, x faces, the four corner columns
+        for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});
+        for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[1], zs[2]});
+        for (int yb = 0; yb < 3; yb += 2)
+            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[1], zs[2]});
     }
+    if ((int)boxes.size() > kMaxSlab) { fdtd_destroy(c); return fail(FDTD_EINVAL, "internal: too many slab boxes"); }
     h.n_slab = 0;
     int blocks = 0;
     for (const auto &bx : boxes) {
@@ -850,9 +865,13 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
             // E: D recurrence along w1, E recurrence along w2 (integer), D->E along w (half)
             // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
             // An auxiliary is needed where D->E (B->H) is graded or both
-            // recurrences are; otherwise the lossy form holds exactly.
+            // recurrences are; otherwise the lossy form holds exactly.  With
+            // 16-bit field storage every slab component keeps its FP32
+            // auxiliary: the lossy form would apply the per-step UPML decay to
+            // the stored 16-bit value, where decrements below half an ulp are
+            // lost, while the auxiliary recurrence carries them in FP32.
             const int rec = is_h ? 1 : 0;
-            const bool need = any_nontrivial(w, is_h ? 0 : 1, false, true) ||
+            const bool need = c->prec != FDTD_FP32 || any_nontrivial(w, is_h ? 0 : 1, false, true) ||
                               (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
             sl.aux[comp] = nullptr;
             if (need && !r) {

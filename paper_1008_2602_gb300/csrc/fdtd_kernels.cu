@@ -822,11 +822,98 @@ __device__ __forceinline__ float upml_e(float e, float scurl, float ce, const Co
 
 // The slab kernels issue every load of a node unconditionally, with the
 // offsets of neighbours that do not exist (i = nx, j = ny, k = nz, or the
-// image across an outer wall) clamped to an in-bounds node, so all of a
-// column's loads can be in flight together; only the stores are conditional.
-template <typename T>
-__global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
+// image across an outer wall) clamped to an in-bounds node; only the stores
+// are conditional.  A thread streams the inputs of its next nodes into a
+// per-thread ring of shared-memory slots with cp.async (one commit group
+// per node), so several nodes' loads are in flight while it updates the
+// current one, without holding them in registers.
+
+// cp.async of the 32-bit word at src (4-byte aligned) into shared memory.
+__device__ __forceinline__ void cp_word(float *dst, const void *src)
 {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Storage element <-> 32-bit word: a 16-bit element is copied with its
+// neighbour (the aligned word holding it) and picked by its index parity.
+// Field arrays start 128-byte aligned and node offsets keep the element
+// index, so the parity of the node index selects the half.
+template <typename T>
+struct Word;
+template <>
+struct Word<float> {
+    static __device__ __forceinline__ const void *at(const float *p) { return p; }
+    static __device__ __forceinline__ float get(float w, long long) { return w; }
+};
+template <>
+struct Word<__half> {
+    static __device__ __forceinline__ const void *at(const __half *p)
+    {
+        return (const void *)((uintptr_t)p & ~(uintptr_t)3);
+    }
+    static __device__ __forceinline__ float get(float w, long long e)
+    {
+        const unsigned b = __float_as_uint(w);
+        return __half2float(__ushort_as_half((unsigned short)((e & 1) ? b >> 16 : b & 0xffffu)));
+    }
+};
+template <>
+struct Word<__nv_bfloat16> {
+    static __device__ __forceinline__ const void *at(const __nv_bfloat16 *p)
+    {
+        return (const void *)((uintptr_t)p & ~(uintptr_t)3);
+    }
+    static __device__ __forceinline__ float get(float w, long long e)
+    {
+        const unsigned b = __float_as_uint(w);
+        return __uint_as_float((e & 1) ? (b & 0xffff0000u) : (b << 16));
+    }
+};
+
+// Coefficient id of node idx from the word holding it (8- or 16-bit ids).
+__device__ __forceinline__ const void *cid_word(const Board *B, long long idx)
+{
+    return B->id16 ? (const void *)((uintptr_t)((const uint16_t *)B->cid + idx) & ~(uintptr_t)3)
+                   : (const void *)((uintptr_t)((const uint8_t *)B->cid + idx) & ~(uintptr_t)3);
+}
+__device__ __forceinline__ int cid_get(const Board *B, float w, long long idx)
+{
+    const unsigned b = __float_as_uint(w);
+    return B->id16 ? (int)((idx & 1) ? b >> 16 : b & 0xffffu) : (int)((b >> (8 * (int)(idx & 3))) & 0xffu);
+}
+
+// Ring slots per thread (nodes in flight + 1), words per node and resident
+// blocks per SM of the two slab kernels; the rings are sized so that the
+// blocks' shared memory fits an SM.
+constexpr int kSlabHStages = 4, kSlabHWords = 15, kSlabHBlocks = 3;
+constexpr int kSlabEStages = 4, kSlabEWords = 19, kSlabEBlocks = 2;
+constexpr int kSlabHSmem = kSlabHStages * kSlabHWords * kSlabThreads * 4;
+constexpr int kSlabESmem = kSlabEStages * kSlabEWords * kSlabThreads * 4;
+static_assert(kSlabHBlocks * (kSlabHSmem + 1024) <= 232448 && kSlabEBlocks * (kSlabESmem + 1024) <= 232448,
+              "slab rings exceed an SM's shared memory");
+
+// Slot w of node m in a thread's ring of S slots of NW words (words of one
+// slot are kSlabThreads apart, so a warp's accesses to a word are conflict-free).
+template <int S, int NW>
+__device__ __forceinline__ float *ring_at(float *my, int m, int w)
+{
+    return my + ((m % S) * NW + w) * kSlabThreads;
+}
+
+enum SlabHWord { hEYC, hEXC, hEYU, hEXU, hEZC, hEZJ, hEZI, hEYI, hEXJ, hHX, hHY, hHZ, hBX, hBY, hBZ };
+
+template <typename T>
+__global__ void __launch_bounds__(kSlabThreads, kSlabHBlocks) k_slab_h(Plan plan)
+{
+    extern __shared__ float slab_ring[];
+    float *const my = slab_ring + threadIdx.x;
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
         SlabCol sc;
@@ -842,64 +929,102 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_h(Plan plan)
         const int di = xin ? 1 : 0;   // clamped +x neighbour offset
         // x factors fixed along the column: H_x (x integer), H_y, H_z (x half)
         const Coef x0 = B->cw[0][0][i], x1 = B->cw[0][1][i];
-        int j = sc.j, k = sc.k;
-        long long idx = (long long)k * P + (long long)j * X + i;
-        long long t = sc.t;
-        const long long didx = sc.ym ? X : P;
-        // E_y, E_x of the current node; marching z, the (k+1) loads become the next node's
-        float eyc = Io<T>::ld(F.ey + idx);
-        float exc = Io<T>::ld(F.ex + idx);
+        const int j0 = sc.j, k0 = sc.k, cnt = sc.count;
+        const bool ym = sc.ym;
+        const long long idx0 = (long long)k0 * P + (long long)j0 * X + i;
+        const long long didx = ym ? X : P;
+        // issue the loads of node m (empty group past the column's end)
+        auto issue = [&](int m) {
+            if (m < cnt) {
+                const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
+                const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
+                const int dj = j < ny ? X : 0;
+                const long long dk = k < nz ? P : 0;
+                if (ym || m == 0) {   // marching z, E_y and E_x at the node are the previous +z loads
+                    cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEYC), Word<T>::at(F.ey + idx));
+                    cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEXC), Word<T>::at(F.ex + idx));
+                }
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEYU), Word<T>::at(F.ey + idx + dk));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEXU), Word<T>::at(F.ex + idx + dk));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEZC), Word<T>::at(F.ez + idx));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEZJ), Word<T>::at(F.ez + idx + dj));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEZI), Word<T>::at(F.ez + idx + di));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEYI), Word<T>::at(F.ey + idx + di));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hEXJ), Word<T>::at(F.ex + idx + dj));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hHX), Word<T>::at(F.hx + idx));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hHY), Word<T>::at(F.hy + idx));
+                cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hHZ), Word<T>::at(F.hz + idx));
+                if (ax) cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hBX), ax + t);
+                if (ay) cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hBY), ay + t);
+                if (az) cp_word(ring_at<kSlabHStages, kSlabHWords>(my, m, hBZ), az + t);
+            }
+            cp_commit();
+        };
+#pragma unroll
+        for (int m = 0; m < kSlabHStages - 1; ++m) issue(m);
+        float eyc = 0.f, exc = 0.f;   // E_y, E_x at the node (carried along z)
 #pragma unroll
         for (int m = 0; m < kSlabKz; ++m) {
-            if (m >= sc.count) break;
-            if (sc.ym && m > 0) {
-                eyc = Io<T>::ld(F.ey + idx);
-                exc = Io<T>::ld(F.ex + idx);
+            if (m >= cnt) break;
+            issue(m + kSlabHStages - 1);
+            cp_wait<kSlabHStages - 1>();
+            const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
+            const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
+            const int dj = j < ny ? X : 0;
+            const long long dk = k < nz ? P : 0;
+            auto w = [&](int word) { return *ring_at<kSlabHStages, kSlabHWords>(my, m, word); };
+            if (ym || m == 0) {
+                eyc = Word<T>::get(w(hEYC), idx);
+                exc = Word<T>::get(w(hEXC), idx);
             }
+            const float eyu = Word<T>::get(w(hEYU), idx + dk), exu = Word<T>::get(w(hEXU), idx + dk);
+            const float ezc = Word<T>::get(w(hEZC), idx);
+            const float ezj = Word<T>::get(w(hEZJ), idx + dj), ezi = Word<T>::get(w(hEZI), idx + di);
+            const float eyi = Word<T>::get(w(hEYI), idx + di), exj = Word<T>::get(w(hEXJ), idx + dj);
+            const float hxo = Word<T>::get(w(hHX), idx), hyo = Word<T>::get(w(hHY), idx);
+            const float hzo = Word<T>::get(w(hHZ), idx);
             const bool yin = j < ny, zin = k < nz;
-            const int dj = yin ? X : 0;   // clamped +y, +z neighbour offsets
-            const long long dk = zin ? P : 0;
-            const float eyu = Io<T>::ld(F.ey + idx + dk), exu = Io<T>::ld(F.ex + idx + dk);
-            const float ezc = Io<T>::ld(F.ez + idx);
-            const float ezj = Io<T>::ld(F.ez + idx + dj), ezi = Io<T>::ld(F.ez + idx + di);
-            const float eyi = Io<T>::ld(F.ey + idx + di), exj = Io<T>::ld(F.ex + idx + dj);
-            const float hxo = Io<T>::ld(F.hx + idx), hyo = Io<T>::ld(F.hy + idx), hzo = Io<T>::ld(F.hz + idx);
-            const float bxo = ax ? ax[t] : 0.f, byo = ay ? ay[t] : 0.f, bzo = az ? az[t] : 0.f;
             const Coef y1 = B->cw[1][1][j], y0 = B->cw[1][0][j], z1 = B->cw[2][1][k], z0 = B->cw[2][0][k];
             float bn;
             if (yin && zin) {   // H_x(i, j+1/2, k+1/2)
-                const float h = upml_h2(hxo, curl2(ezj, ezc, eyu, eyc, Sy, Sz), y1, z1, x0, ax != nullptr, bxo, bn);
+                const float h = upml_h2(hxo, curl2(ezj, ezc, eyu, eyc, Sy, Sz), y1, z1, x0, ax != nullptr,
+                                        ax ? w(hBX) : 0.f, bn);
                 Io<T>::st(F.ohx + idx, h);
                 if (ax) ax[t] = bn;
             }
             if (xin && zin) {   // H_y(i+1/2, j, k+1/2)
-                const float h = upml_h2(hyo, curl2(exu, exc, ezi, ezc, Sz, Sx), z1, x1, y0, ay != nullptr, byo, bn);
+                const float h = upml_h2(hyo, curl2(exu, exc, ezi, ezc, Sz, Sx), z1, x1, y0, ay != nullptr,
+                                        ay ? w(hBY) : 0.f, bn);
                 Io<T>::st(F.ohy + idx, h);
                 if (ay) ay[t] = bn;
             }
             if (xin && yin) {   // H_z(i+1/2, j+1/2, k)
-                const float h = upml_h2(hzo, curl2(eyi, eyc, exj, exc, Sx, Sy), x1, y1, z0, az != nullptr, bzo, bn);
+                const float h = upml_h2(hzo, curl2(eyi, eyc, exj, exc, Sx, Sy), x1, y1, z0, az != nullptr,
+                                        az ? w(hBZ) : 0.f, bn);
                 Io<T>::st(F.ohz + idx, h);
                 if (az) az[t] = bn;
             }
             eyc = eyu;
             exc = exu;
-            idx += didx;
-            t += sc.tstep;
-            if (sc.ym) ++j; else ++k;
         }
+        cp_wait<0>();   // no copy into the ring may be outstanding when the next block reuses it
     }
 }
 
-// Offset of H~ at a neighbour `in` or, when it lies `outside` the grid, of its
-// image `mirror` across the wall; wall_sign gives the image's factor (PMC:
-// odd mirror of tangential H, -1; PEC: 0).
-__device__ __forceinline__ long long hoff(bool outside, long long in, long long mirror) { return outside ? mirror : in; }
+// Factor of the image of tangential H~ across an outer wall for a neighbour
+// `outside` the grid (PMC: odd mirror, -1; PEC: 0).
 __device__ __forceinline__ float hsign(bool outside, int wall) { return outside ? (wall == 1 ? -1.0f : 0.0f) : 1.0f; }
 
+enum SlabEWord {
+    eHZY1, eHZY0, eHYZ1, eHYZ0, eHXZ1, eHXZ0, eHZX1, eHZX0, eHYX1, eHYX0, eHXY1, eHXY0,
+    eEX, eEY, eEZ, eDX, eDY, eDZ, eID
+};
+
 template <typename T>
-__global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
+__global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan)
 {
+    extern __shared__ float slab_ring[];
+    float *const my = slab_ring + threadIdx.x;
     for (long long blk = blockIdx.x; blk < plan.n_slab; blk += gridDim.x) {
         const Board *B;
         SlabCol sc;
@@ -912,59 +1037,102 @@ __global__ void __launch_bounds__(kSlabThreads) k_slab_e(Plan plan)
         const float Sx = B->S[0], Sy = B->S[1], Sz = B->S[2];
         const Slab &sl = *sc.sl;
         float *const ax = sl.aux[0], *const ay = sl.aux[1], *const az = sl.aux[2];
-        const int *w = B->wall;
-        const int w2 = w[2], w3 = w[3], w4 = w[4], w5 = w[5];
+        const int *wl = B->wall;
+        const int w2 = wl[2], w3 = wl[3], w4 = wl[4], w5 = wl[5];
         // images across the x walls (fixed along the column)
         const bool xhi = i == nx, xlo = i == 0;
-        const float sxh = hsign(xhi, w[1]), sxl = hsign(xlo, w[0]);
+        const float sxh = hsign(xhi, wl[1]), sxl = hsign(xlo, wl[0]);
         const int ox1 = xhi ? -1 : 0, ox0 = xlo ? 0 : -1;   // offsets of H at i and i-1 (or images)
         // x factors fixed along the column: E_x (x half), E_y, E_z (x integer)
         const Coef x1 = B->cw[0][1][i], x0 = B->cw[0][0][i];
-        int j = sc.j, k = sc.k;
-        long long idx = (long long)k * P + (long long)j * X + i;
-        long long t = sc.t;
-        const long long didx = sc.ym ? X : P;
+        const int j0 = sc.j, k0 = sc.k, cnt = sc.count;
+        const bool ym = sc.ym;
+        const long long idx0 = (long long)k0 * P + (long long)j0 * X + i;
+        const long long didx = ym ? X : P;
+        auto issue = [&](int m) {
+            if (m < cnt) {
+                const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
+                const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
+                const int oy1 = j == ny ? -X : 0, oy0 = j == 0 ? 0 : -X;
+                const long long oz1 = k == nz ? -P : 0, oz0 = k == 0 ? 0 : -P;
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eID), cid_word(B, idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY1), Word<T>::at(F.ohz + idx + oy1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY0), Word<T>::at(F.ohz + idx + oy0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYZ1), Word<T>::at(F.ohy + idx + oz1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXZ1), Word<T>::at(F.ohx + idx + oz1));
+                if (ym || m == 0) {   // marching z, H~y and H~x at -z are the previous node's values
+                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYZ0), Word<T>::at(F.ohy + idx + oz0));
+                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXZ0), Word<T>::at(F.ohx + idx + oz0));
+                }
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZX1), Word<T>::at(F.ohz + idx + ox1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZX0), Word<T>::at(F.ohz + idx + ox0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYX1), Word<T>::at(F.ohy + idx + ox1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYX0), Word<T>::at(F.ohy + idx + ox0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXY1), Word<T>::at(F.ohx + idx + oy1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXY0), Word<T>::at(F.ohx + idx + oy0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEX), Word<T>::at(F.ex + idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEY), Word<T>::at(F.ey + idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEZ), Word<T>::at(F.ez + idx));
+                if (ax) cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eDX), ax + t);
+                if (ay) cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eDY), ay + t);
+                if (az) cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eDZ), az + t);
+            }
+            cp_commit();
+        };
+#pragma unroll
+        for (int m = 0; m < kSlabEStages - 1; ++m) issue(m);
+        float hyz0 = 0.f, hxz0 = 0.f;   // raw H~y, H~x at -z (carried along z)
 #pragma unroll
         for (int m = 0; m < kSlabKz; ++m) {
-            if (m >= sc.count) break;
+            if (m >= cnt) break;
+            issue(m + kSlabEStages - 1);
+            cp_wait<kSlabEStages - 1>();
+            const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
+            const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
+            const int oy1 = j == ny ? -X : 0, oy0 = j == 0 ? 0 : -X;
+            const long long oz1 = k == nz ? -P : 0, oz0 = k == 0 ? 0 : -P;
+            auto w = [&](int word) { return *ring_at<kSlabEStages, kSlabEWords>(my, m, word); };
             const bool yhi = j == ny, ylo = j == 0, zhi = k == nz, zlo = k == 0;
             const float syh = hsign(yhi, w3), syl = hsign(ylo, w2), szh = hsign(zhi, w5), szl = hsign(zlo, w4);
-            const int oy1 = yhi ? -X : 0, oy0 = ylo ? 0 : -X;
-            const long long oz1 = zhi ? -P : 0, oz0 = zlo ? 0 : -P;
-            const float4 ce = __ldg(B->ctab + cid_at(B, idx));
+            const float4 ce = __ldg(B->ctab + cid_get(B, w(eID), idx));
             const Coef y0 = B->cw[1][0][j], y1 = B->cw[1][1][j], z0 = B->cw[2][0][k], z1 = B->cw[2][1][k];
-            // H~ at the node and its -x, -y, -z neighbours (or their images)
-            const float hz_y1 = syh * Io<T>::ld(F.ohz + idx + oy1), hz_y0 = syl * Io<T>::ld(F.ohz + idx + oy0);
-            const float hy_z1 = szh * Io<T>::ld(F.ohy + idx + oz1), hy_z0 = szl * Io<T>::ld(F.ohy + idx + oz0);
-            const float hx_z1 = szh * Io<T>::ld(F.ohx + idx + oz1), hx_z0 = szl * Io<T>::ld(F.ohx + idx + oz0);
-            const float hz_x1 = sxh * Io<T>::ld(F.ohz + idx + ox1), hz_x0 = sxl * Io<T>::ld(F.ohz + idx + ox0);
-            const float hy_x1 = sxh * Io<T>::ld(F.ohy + idx + ox1), hy_x0 = sxl * Io<T>::ld(F.ohy + idx + ox0);
-            const float hx_y1 = syh * Io<T>::ld(F.ohx + idx + oy1), hx_y0 = syl * Io<T>::ld(F.ohx + idx + oy0);
-            const float exo = Io<T>::ld(F.ex + idx), eyo = Io<T>::ld(F.ey + idx), ezo = Io<T>::ld(F.ez + idx);
-            const float dxo = ax ? ax[t] : 0.f, dyo = ay ? ay[t] : 0.f, dzo = az ? az[t] : 0.f;
+            if (ym || m == 0) {
+                hyz0 = Word<T>::get(w(eHYZ0), idx + oz0);
+                hxz0 = Word<T>::get(w(eHXZ0), idx + oz0);
+            }
+            const float hyz1 = Word<T>::get(w(eHYZ1), idx + oz1), hxz1 = Word<T>::get(w(eHXZ1), idx + oz1);
             float dn;
             if (i < nx) {   // E_x(i+1/2, j, k)
-                const float e = upml_e2(exo, curl2(hz_y1, hz_y0, hy_z1, hy_z0, Sy, Sz), ce.x, y0, z0, x1,
-                                        ax != nullptr, dxo, dn);
+                const float e = upml_e2(Word<T>::get(w(eEX), idx),
+                                        curl2(syh * Word<T>::get(w(eHZY1), idx + oy1),
+                                              syl * Word<T>::get(w(eHZY0), idx + oy0), szh * hyz1, szl * hyz0, Sy,
+                                              Sz),
+                                        ce.x, y0, z0, x1, ax != nullptr, ax ? w(eDX) : 0.f, dn);
                 Io<T>::st(F.oex + idx, e);
                 if (ax) ax[t] = dn;
             }
             if (j < ny) {   // E_y(i, j+1/2, k)
-                const float e = upml_e2(eyo, curl2(hx_z1, hx_z0, hz_x1, hz_x0, Sz, Sx), ce.y, z0, x0, y1,
-                                        ay != nullptr, dyo, dn);
+                const float e = upml_e2(Word<T>::get(w(eEY), idx),
+                                        curl2(szh * hxz1, szl * hxz0, sxh * Word<T>::get(w(eHZX1), idx + ox1),
+                                              sxl * Word<T>::get(w(eHZX0), idx + ox0), Sz, Sx),
+                                        ce.y, z0, x0, y1, ay != nullptr, ay ? w(eDY) : 0.f, dn);
                 Io<T>::st(F.oey + idx, e);
                 if (ay) ay[t] = dn;
             }
             if (k < nz) {   // E_z(i, j, k+1/2)
-                const float e = upml_e2(ezo, curl2(hy_x1, hy_x0, hx_y1, hx_y0, Sx, Sy), ce.z, x0, y0, z1,
-                                        az != nullptr, dzo, dn);
+                const float e = upml_e2(Word<T>::get(w(eEZ), idx),
+                                        curl2(sxh * Word<T>::get(w(eHYX1), idx + ox1),
+                                              sxl * Word<T>::get(w(eHYX0), idx + ox0),
+                                              syh * Word<T>::get(w(eHXY1), idx + oy1),
+                                              syl * Word<T>::get(w(eHXY0), idx + oy0), Sx, Sy),
+                                        ce.z, x0, y0, z1, az != nullptr, az ? w(eDZ) : 0.f, dn);
                 Io<T>::st(F.oez + idx, e);
                 if (az) az[t] = dn;
             }
-            idx += didx;
-            t += sc.tstep;
-            if (sc.ym) ++j; else ++k;
+            hyz0 = hyz1;   // the next node (k + 1 <= nz) reads H at k, which this node read unclamped
+            hxz0 = hxz1;
         }
+        cp_wait<0>();
     }
 }
 
@@ -1248,7 +1416,7 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
     switch (phase) {
     case kPhaseSlabH:
         if (plan.n_slab > 0)
-            k_slab_h<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, 0, st>>>(plan);
+            k_slab_h<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, kSlabHSmem, st>>>(plan);
         break;
     case kPhaseFusedZ:
         if (plan.n_zp > 0) {
@@ -1264,7 +1432,7 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
         break;
     case kPhaseSlabE:
         if (plan.n_slab > 0)
-            k_slab_e<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, 0, st>>>(plan);
+            k_slab_e<T><<<(int)(plan.n_slab < kMaxGrid ? plan.n_slab : kMaxGrid), kSlabThreads, kSlabESmem, st>>>(plan);
         break;
     default:
         k_post<T><<<plan.nb, 128, 0, st>>>(plan);
@@ -1296,7 +1464,8 @@ bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (t
 template <typename T>
 static cudaError_t limits_t()
 {
-    cudaError_t e[8] = {FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 2>::set_limit(),
+    cudaError_t e[10] = {cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
+                        cudaFuncSetAttribute(k_slab_e<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabESmem),FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 2>::set_limit(),
                         FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),
                         FusedCfg<T, 4, 1, true, 1>::set_limit(),  FusedCfg<T, 8, 1, true, 2>::set_limit(),
                         FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit()};
