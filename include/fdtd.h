@@ -308,12 +308,13 @@ int fdtd_batch_sync(fdtd_batch *b);
 void fdtd_batch_destroy(fdtd_batch *b);
 
 /* Tuning knobs of the kernels (autotuner): the fused-kernel tile (tile_x
- * columns: 62 or 124, i.e. one or two compute warps of 62 columns; tile_y
- * rows: 4 or 8, an 8-row tile being two compute warps of 4 rows; default
- * 62x8 in FP32, 124x8 with 16-bit storage), the
- * z-segment length (planes one tile marches before the next work item;
- * default 10) and the number of steps per CUDA graph (default 16).  Values <= 0 keep the current setting; unsupported tiles are
- * rejected with FDTD_EINVAL.  Applies to launches queued afterwards. */
+ * columns: 62 or 124, i.e. one or two strips of 62 columns; tile_y rows: 4
+ * or 8; a 62x8 tile is worked by four compute warps of 2 rows, a 124x8 tile
+ * by two warps of 4 rows per strip; default 62x8), the z-segment length
+ * (planes one tile marches before the next work item; default 10) and the
+ * number of steps per CUDA graph (default 16).  Values <= 0 keep the current
+ * setting; unsupported tiles are rejected with FDTD_EINVAL.  Applies to
+ * launches queued afterwards. */
 typedef struct {
     int tile_x, tile_y, zseg, graph_chunk;
 } fdtd_tuning;

@@ -116,7 +116,6 @@ struct fdtd_batch {
     std::vector<fdtd_ctx *> members;
     std::vector<long long> remaining;
     fdtd_tuning tune{62, 8, 10, 16};
-    bool tuned = false;             // set_tuning called: keep the caller's tile
     bool dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;
@@ -735,10 +734,6 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     if (n_pec > 0) c->boxes.assign(pec, pec + n_pec);
     if (pec_mask) c->mask.assign(pec_mask, pec_mask + (size_t)grid->nx * grid->ny * grid->nz);
     c->prec = precision;
-    // default fused tile: 62x8 (two compute warps of four rows sharing a
-    // stage); 16-bit stages are half as large, so 124x8 (four compute warps)
-    // fits as many blocks per SM
-    if (precision != FDTD_FP32) c->tune.tile_x = 124;
     c->dt = grid->dt > 0 ? grid->dt
                          : grid->courant / (kC0 * std::sqrt(1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dy * grid->dy) +
                                                              1.0 / (grid->dz * grid->dz)));
@@ -1447,7 +1442,6 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t)
     if (!fused_tile_supported(n.tile_x, n.tile_y))
         return fail(FDTD_EINVAL, "fused tile (tile_x x tile_y) must be 62x4, 62x8, 124x4 or 124x8");
     b->tune = n;
-    b->tuned = true;
     b->dirty = true;
     return FDTD_OK;
 }
@@ -1466,7 +1460,6 @@ int fdtd_batch_add(fdtd_batch *b, fdtd_ctx *c, int n_steps)
     c->batch = b;
     b->members.push_back(c);
     b->remaining.push_back(n_steps);
-    if (b->prec < 0 && !b->tuned && c->prec != FDTD_FP32) b->tune.tile_x = 124;   // as for a single board
     b->prec = c->prec;
     b->dirty = true;
     return FDTD_OK;

@@ -340,10 +340,12 @@ struct FusedLayout {
     static constexpr int BAR_OFF = NS * St::BYTES;
     static constexpr int BYTES = BAR_OFF + 2 * NS * 8 + 16;
     // blocks per SM that shared memory allows (227 KB usable per SM, 1 KB
-    // reserved per block); the register budget keeps them resident but never drops
-    // below 128 registers per thread (176 for 8-row tiles)
+    // reserved per block); the register budget keeps them resident but never
+    // drops below a per-thread floor that the warp's row count sets: 176 for
+    // 8 rows, 168 (z-UPML) or 128 for 4 rows, 136 (z-UPML) or 96 for 2 rows
+    static constexpr int REG_FLOOR = TY / R >= 8 ? 176 : (TY / R >= 4 ? (ZP ? 168 : 128) : (ZP ? 136 : 96));
     static constexpr int PER_SM = 232448 / (BYTES + 1024);
-    static constexpr int REG_SM = 65536 / ((TY / R >= 8 ? 176 : (ZP ? 168 : 128)) * (32 * W * R + 32));
+    static constexpr int REG_SM = 65536 / (REG_FLOOR * (32 * W * R + 32));
     static constexpr int CAP = PER_SM < REG_SM ? PER_SM : REG_SM;
     static constexpr int MINB = CAP < 1 ? 1 : (CAP > 8 ? 8 : CAP);
 };
@@ -1393,14 +1395,14 @@ struct FusedCfg {
 };
 
 // Supported fused tiles (tile_x columns x tile_y rows): 62x4 and 124x4 (one
-// compute warp per 62 columns), 62x8 and 124x8 (two compute warps of four
-// rows per 62 columns, sharing the stage).
+// compute warp per 62 columns), 62x8 (four compute warps of two rows sharing
+// the stage) and 124x8 (two compute warps of four rows per 62 columns).
 template <typename T, bool ZP>
 static void launch_fused(const Plan &plan, cudaStream_t st)
 {
     const int key = plan.tile_x * 16 + plan.tile_y;
     switch (key) {
-    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP, 2>::launch(plan, st); break;
+    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP, 4>::launch(plan, st); break;
     case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP, 1>::launch(plan, st); break;
     case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP, 2>::launch(plan, st); break;
     default: FusedCfg<T, 4, 1, ZP, 1>::launch(plan, st); break;
@@ -1465,10 +1467,11 @@ template <typename T>
 static cudaError_t limits_t()
 {
     cudaError_t e[10] = {cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
-                        cudaFuncSetAttribute(k_slab_e<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabESmem),FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 2>::set_limit(),
-                        FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),
-                        FusedCfg<T, 4, 1, true, 1>::set_limit(),  FusedCfg<T, 8, 1, true, 2>::set_limit(),
-                        FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit()};
+                         cudaFuncSetAttribute(k_slab_e<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabESmem),
+                         FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 4>::set_limit(),
+                         FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),
+                         FusedCfg<T, 4, 1, true, 1>::set_limit(),  FusedCfg<T, 8, 1, true, 4>::set_limit(),
+                         FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit()};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;
