@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <array>
 #include <climits>
+#include <memory>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -209,48 +210,110 @@ void build_axes(const fdtd_ctx *c, Axes &A)
 // on edges that do not exist.  Returns the table (<= 65536 rows) and the
 // pitched id volume; the caller stores ids as uint8 when the table has at most
 // 256 rows.
-int build_combo(const fdtd_ctx *c, const uint8_t *mat, std::vector<uint16_t> &cid, std::vector<float4> &table)
+// Node coefficient ids of a geometry.  Plane-local ids are assigned in
+// parallel over planes and merged into one table; the ids go to `cid`
+// (uint16) or, when the table has at most kMaxCombo rows, straight to `c8`.
+struct NodeIds {
+    std::unique_ptr<uint16_t[]> cid;   // [nodes], also the plane-local ids before the merge
+    std::unique_ptr<uint8_t[]> c8;     // [nodes] when the merged table fits 8-bit ids
+    size_t n = 0;
+};
+
+int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector<float4> &table)
 {
     const int nx = c->g.nx, ny = c->g.ny, nz = c->g.nz;
     const int NX = nx + 1, NY = ny + 1, NZ = nz + 1;
     const int pitch = c->h.pitch;
-    for (size_t t = 0; t < (size_t)nx * ny * nz; ++t)
-        if (mat[t] >= c->eps.size()) return fail(FDTD_EINVAL, "material id out of range of eps_r");
+    const long long ncell = (long long)nx * ny * nz;
+    const int neps = (int)c->eps.size();
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(| : bad)
+    for (long long t = 0; t < ncell; ++t) bad |= mat[t] >= neps;
+    if (bad) return fail(FDTD_EINVAL, "material id out of range of eps_r");
     // PEC edge bits per node: 1 = x edge, 2 = y edge, 4 = z edge
-    std::vector<uint8_t> pec((size_t)NX * NY * NZ, 0);
-    auto mark_box = [&](int i0, int i1, int j0, int j1, int k0, int k1) {
-        for (int k = std::max(k0, 0); k <= std::min(k1, nz); ++k)
-            for (int j = std::max(j0, 0); j <= std::min(j1, ny); ++j)
-                for (int i = std::max(i0, 0); i <= std::min(i1, nx); ++i) {
-                    uint8_t bits = 0;
-                    if (i < i1 && i < nx) bits |= 1;
-                    if (j < j1 && j < ny) bits |= 2;
-                    if (k < k1 && k < nz) bits |= 4;
-                    pec[((size_t)k * NY + j) * NX + i] |= bits;
-                }
+    const size_t nnode = (size_t)NX * NY * NZ;
+    std::unique_ptr<uint8_t[]> pec(new uint8_t[nnode]);
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < NZ; ++k) std::memset(pec.get() + (size_t)k * NY * NX, 0, (size_t)NY * NX);
+    // rows of one box are disjoint, so a box is marked in parallel over its rows
+    auto mark_box = [&](int i0, int i1, int j0, int j1, int k0, int k1, bool par) {
+        const int ka = std::max(k0, 0), kb = std::min(k1, nz), ja = std::max(j0, 0), jb = std::min(j1, ny);
+        const int rows = (kb - ka + 1) * (jb - ja + 1);
+#pragma omp parallel for schedule(static) if (par && rows > 64)
+        for (int r = 0; r < rows; ++r) {
+            const int k = ka + r / (jb - ja + 1), j = ja + r % (jb - ja + 1);
+            for (int i = std::max(i0, 0); i <= std::min(i1, nx); ++i) {
+                uint8_t bits = 0;
+                if (i < i1 && i < nx) bits |= 1;
+                if (j < j1 && j < ny) bits |= 2;
+                if (k < k1 && k < nz) bits |= 4;
+                pec[((size_t)k * NY + j) * NX + i] |= bits;
+            }
+        }
     };
-    for (const fdtd_box &b : c->boxes) mark_box(b.i0, b.i1, b.j0, b.j1, b.k0, b.k1);
+    for (const fdtd_box &b : c->boxes) mark_box(b.i0, b.i1, b.j0, b.j1, b.k0, b.k1, true);
     if (!c->mask.empty())
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i)
-                    if (c->mask[((size_t)k * ny + j) * nx + i]) mark_box(i, i + 1, j, j + 1, k, k + 1);
+                    if (c->mask[((size_t)k * ny + j) * nx + i]) mark_box(i, i + 1, j, j + 1, k, k + 1, false);
     const int *wall = c->bnd.wall;
 
-    cid.assign((size_t)pitch * NY * NZ, 0);
+    ids.n = (size_t)pitch * NY * NZ;
+    ids.cid.reset(new uint16_t[ids.n]);
+    ids.c8.reset();
+    uint16_t *const cid = ids.cid.get();
     std::vector<std::vector<float4>> plane_tab(NZ);
     std::vector<int> overflow(NZ, 0);
     std::vector<std::unordered_map<uint64_t, uint32_t>> plane_map(NZ);
     auto eps_cell = [&](int i, int j, int k) { return c->eps[mat[((size_t)k * ny + j) * nx + i]]; };
+    // A node whose eight cells share one material, away from walls and PEC,
+    // has all three edges at 1/eps of it: the general sums below reduce to
+    // ((e + e) + e) + e over four cells, so this table gives the same floats.
+    std::vector<float> ce_uniform(neps);
+    for (int m = 0; m < neps; ++m) {
+        const double e = c->eps[m];
+        ce_uniform[m] = (float)(4 / (((e + e) + e) + e));
+    }
+    const size_t sx = (size_t)nx, sxy = (size_t)nx * ny;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < NZ; ++k) {
         std::vector<float4> &tab = plane_tab[k];
         std::unordered_map<uint64_t, uint32_t> &map = plane_map[k];
         float4 last = make_float4(-1, -1, -1, 0);
         uint16_t last_id = 0;
+        // 1/mean(eps) of an edge from its n adjacent cells' sum s; neighbouring
+        // edges mostly repeat (n, s), so the last quotient per direction is kept
+        double qs[3] = {-1.0, -1.0, -1.0};
+        int qn[3] = {0, 0, 0};
+        float qv[3] = {0.f, 0.f, 0.f};
+        auto quot = [&](int d, int n, double sum) {
+            if (sum != qs[d] || n != qn[d]) {
+                qs[d] = sum;
+                qn[d] = n;
+                qv[d] = (float)(n / sum);
+            }
+            return qv[d];
+        };
         for (int j = 0; j < NY; ++j) {
+            for (int i = NX; i < pitch; ++i) cid[((size_t)k * NY + j) * pitch + i] = 0;   // row padding
+            const bool inner_row = j >= 1 && j < ny && k >= 1 && k < nz;
+            const uint8_t *m00 = inner_row ? mat + (size_t)(k - 1) * sxy + (size_t)(j - 1) * sx : nullptr;
             for (int i = 0; i < NX; ++i) {
                 const uint8_t pb = pec[((size_t)k * NY + j) * NX + i];
+                if (inner_row && i >= 1 && i < nx && pb == 0) {
+                    // cells (i-1..i, j-1..j, k-1..k)
+                    const uint8_t *q = m00 + (i - 1);
+                    const uint8_t m = q[0];
+                    if (q[1] == m && q[sx] == m && q[sx + 1] == m && q[sxy] == m && q[sxy + 1] == m &&
+                        q[sxy + sx] == m && q[sxy + sx + 1] == m) {
+                        const float u = ce_uniform[m];
+                        if (u == last.x && u == last.y && u == last.z) {
+                            cid[((size_t)k * NY + j) * pitch + i] = last_id;
+                            continue;
+                        }
+                    }
+                }
                 const bool wx = (i == 0 && wall[0] == FDTD_WALL_PEC) || (i == nx && wall[1] == FDTD_WALL_PEC);
                 const bool wy = (j == 0 && wall[2] == FDTD_WALL_PEC) || (j == ny && wall[3] == FDTD_WALL_PEC);
                 const bool wz = (k == 0 && wall[4] == FDTD_WALL_PEC) || (k == nz && wall[5] == FDTD_WALL_PEC);
@@ -260,21 +323,21 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, std::vector<uint16_t> &ci
                     for (int b = k - 1; b <= k; ++b)
                         for (int a = j - 1; a <= j; ++a)
                             if (a >= 0 && a < ny && b >= 0 && b < nz) { s += eps_cell(i, a, b); ++n; }
-                    ce[0] = (float)(n / s);
+                    ce[0] = quot(0, n, s);
                 }
                 if (j < ny && !(pb & 2) && !wx && !wz) {
                     double s = 0; int n = 0;
                     for (int b = k - 1; b <= k; ++b)
                         for (int a = i - 1; a <= i; ++a)
                             if (a >= 0 && a < nx && b >= 0 && b < nz) { s += eps_cell(a, j, b); ++n; }
-                    ce[1] = (float)(n / s);
+                    ce[1] = quot(1, n, s);
                 }
                 if (k < nz && !(pb & 4) && !wx && !wy) {
                     double s = 0; int n = 0;
                     for (int b = j - 1; b <= j; ++b)
                         for (int a = i - 1; a <= i; ++a)
                             if (a >= 0 && a < nx && b >= 0 && b < ny) { s += eps_cell(a, b, k); ++n; }
-                    ce[2] = (float)(n / s);
+                    ce[2] = quot(2, n, s);
                 }
                 const float4 v = make_float4(ce[0], ce[1], ce[2], 0.f);
                 uint16_t id;
@@ -332,11 +395,26 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, std::vector<uint16_t> &ci
             remap[k].push_back((uint16_t)t);
         }
     }
+    if (table.size() <= (size_t)kMaxCombo) {
+        ids.c8.reset(new uint8_t[ids.n]);
+        uint8_t *const c8 = ids.c8.get();
 #pragma omp parallel for schedule(static)
-    for (int k = 0; k < NZ; ++k) {
-        uint16_t *row = cid.data() + (size_t)k * NY * pitch;
-        for (int j = 0; j < NY; ++j)
-            for (int i = 0; i < NX; ++i) row[(size_t)j * pitch + i] = remap[k][row[(size_t)j * pitch + i]];
+        for (int k = 0; k < NZ; ++k) {
+            const uint16_t *row = cid + (size_t)k * NY * pitch;
+            uint8_t *out = c8 + (size_t)k * NY * pitch;
+            for (int j = 0; j < NY; ++j) {
+                for (int i = 0; i < NX; ++i) out[(size_t)j * pitch + i] = (uint8_t)remap[k][row[(size_t)j * pitch + i]];
+                for (int i = NX; i < pitch; ++i) out[(size_t)j * pitch + i] = 0;
+            }
+        }
+        ids.cid.reset();
+    } else {
+#pragma omp parallel for schedule(static)
+        for (int k = 0; k < NZ; ++k) {
+            uint16_t *row = cid + (size_t)k * NY * pitch;
+            for (int j = 0; j < NY; ++j)
+                for (int i = 0; i < NX; ++i) row[(size_t)j * pitch + i] = remap[k][row[(size_t)j * pitch + i]];
+        }
     }
     return FDTD_OK;
 }
@@ -622,9 +700,9 @@ int check_status(fdtd_ctx *c)
 
 int set_geometry(fdtd_ctx *c, const uint8_t *mat)
 {
-    std::vector<uint16_t> cid;
+    NodeIds ids;
     std::vector<float4> table;
-    if (int r = build_combo(c, mat, cid, table)) return r;
+    if (int r = build_combo(c, mat, ids, table)) return r;
     c->n_combo = (int)table.size();
     const int id16 = table.size() > (size_t)kMaxCombo ? 1 : 0;
     const size_t rows = id16 ? (size_t)kMaxCombo16 : (size_t)kMaxCombo;
@@ -643,19 +721,13 @@ int set_geometry(fdtd_ctx *c, const uint8_t *mat)
         c->h.tm_tx = 0;
         c->plan_dirty = true;
     }
-    if (id16) {
-        CK(cudaMemcpyAsync((void *)c->h.cid, cid.data(), cid.size() * 2, cudaMemcpyHostToDevice, c->cur));
-        CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
-        CK(cudaStreamSynchronize(c->cur));
-    } else {
-        std::vector<uint8_t> c8(cid.size());
-#pragma omp parallel for schedule(static)
-        for (long long t = 0; t < (long long)cid.size(); ++t) c8[t] = (uint8_t)cid[t];
-        CK(cudaMemcpyAsync((void *)c->h.cid, c8.data(), c8.size(), cudaMemcpyHostToDevice, c->cur));
-        CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
-        // the host copies stay alive until the copies finish
-        CK(cudaStreamSynchronize(c->cur));
-    }
+    if (id16)
+        CK(cudaMemcpyAsync((void *)c->h.cid, ids.cid.get(), ids.n * 2, cudaMemcpyHostToDevice, c->cur));
+    else
+        CK(cudaMemcpyAsync((void *)c->h.cid, ids.c8.get(), ids.n, cudaMemcpyHostToDevice, c->cur));
+    CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
+    // the host copies stay alive until the copies finish
+    CK(cudaStreamSynchronize(c->cur));
     if (c->d) return upload_board(c);
     return FDTD_OK;
 }
