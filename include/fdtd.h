@@ -116,8 +116,11 @@ typedef struct {
  *  stream    cudaStream_t the context enqueues on; NULL makes the library
  *            create (and later destroy) its own non-blocking stream.
  *  out       receives the context.
- * Errors: FDTD_EINVAL for bad sizes or walls, more than 256 distinct edge
- * coefficient triples, a PMC face with UPML; FDTD_ENOMEM; FDTD_ECUDA. */
+ * The per-node coefficient ids are built as in fdtd_set_materials: uint8
+ * for up to 256 distinct edge coefficient triples, uint16 beyond.
+ * Errors: FDTD_EINVAL for bad sizes or walls, a material id outside eps_r,
+ * more than 65536 distinct edge coefficient triples, a PMC face with UPML;
+ * FDTD_ENOMEM; FDTD_ECUDA. */
 int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat,
                 const fdtd_box *pec, int n_pec, const uint8_t *pec_mask,
                 const fdtd_boundary *bnd, int precision, void *stream, fdtd_ctx **out);
@@ -227,9 +230,12 @@ int fdtd_load(fdtd_ctx *ctx, const void *buf, size_t size);
 int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls);
 
 /* Replace the material ids of the board (same eps_r table, PEC and ports),
- * copying host mat_ids [nz][ny][nx] to the device and rebuilding the edge
- * coefficient ids, then reset.  Returns FDTD_EINVAL if the new geometry has
- * more than 256 coefficient triples. */
+ * rebuilding the per-node edge coefficient ids on the host (in parallel) and
+ * copying them to the device, then reset.  The host id buffers (3 bytes per
+ * node of the largest board seen) are a process-wide scratch kept for reuse;
+ * calls from several threads take turns on it.  Returns FDTD_EINVAL for a
+ * material id outside eps_r or more than 65536 distinct coefficient triples,
+ * FDTD_ENOMEM if the scratch cannot grow. */
 int fdtd_set_materials(fdtd_ctx *ctx, const uint8_t *mat_ids);
 
 /* Fill *info (synchronises to read the step counter). */

@@ -15,6 +15,7 @@
 #include <array>
 #include <climits>
 #include <memory>
+#include <mutex>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -212,12 +213,34 @@ void build_axes(const fdtd_ctx *c, Axes &A)
 // 256 rows.
 // Node coefficient ids of a geometry.  Plane-local ids are assigned in
 // parallel over planes and merged into one table; the ids go to `cid`
-// (uint16) or, when the table has at most kMaxCombo rows, straight to `c8`.
+// (uint16) or, when the table has at most kMaxCombo rows, to `c8`.  The
+// buffers are one process-wide scratch, grown on demand and reused under its
+// lock, so that their pages are first touched once per process rather than
+// once per geometry.
 struct NodeIds {
-    std::unique_ptr<uint16_t[]> cid;   // [nodes], also the plane-local ids before the merge
-    std::unique_ptr<uint8_t[]> c8;     // [nodes] when the merged table fits 8-bit ids
+    uint16_t *cid = nullptr;   // [n], also the plane-local ids before the merge
+    uint8_t *c8 = nullptr;     // [n], valid when `wide` is false
+    bool wide = true;
     size_t n = 0;
 };
+struct IdScratch {
+    std::mutex lock;
+    std::unique_ptr<uint16_t[]> cid;
+    std::unique_ptr<uint8_t[]> c8;
+    size_t cap = 0;
+    void reserve(size_t n)
+    {
+        if (n <= cap) return;
+        cid.reset(new uint16_t[n]);
+        c8.reset(new uint8_t[n]);
+        cap = n;
+    }
+};
+IdScratch &id_scratch()
+{
+    static IdScratch s;
+    return s;
+}
 
 int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector<float4> &table)
 {
@@ -260,21 +283,11 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector
     const int *wall = c->bnd.wall;
 
     ids.n = (size_t)pitch * NY * NZ;
-    ids.cid.reset(new uint16_t[ids.n]);
-    ids.c8.reset();
-    uint16_t *const cid = ids.cid.get();
+    uint16_t *const cid = ids.cid;   // caller-provided, ids.n entries
     std::vector<std::vector<float4>> plane_tab(NZ);
     std::vector<int> overflow(NZ, 0);
     std::vector<std::unordered_map<uint64_t, uint32_t>> plane_map(NZ);
     auto eps_cell = [&](int i, int j, int k) { return c->eps[mat[((size_t)k * ny + j) * nx + i]]; };
-    // A node whose eight cells share one material, away from walls and PEC,
-    // has all three edges at 1/eps of it: the general sums below reduce to
-    // ((e + e) + e) + e over four cells, so this table gives the same floats.
-    std::vector<float> ce_uniform(neps);
-    for (int m = 0; m < neps; ++m) {
-        const double e = c->eps[m];
-        ce_uniform[m] = (float)(4 / (((e + e) + e) + e));
-    }
     const size_t sx = (size_t)nx, sxy = (size_t)nx * ny;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int k = 0; k < NZ; ++k) {
@@ -282,6 +295,7 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector
         std::unordered_map<uint64_t, uint32_t> &map = plane_map[k];
         float4 last = make_float4(-1, -1, -1, 0);
         uint16_t last_id = 0;
+        uint8_t last_pb = 0;
         // 1/mean(eps) of an edge from its n adjacent cells' sum s; neighbouring
         // edges mostly repeat (n, s), so the last quotient per direction is kept
         double qs[3] = {-1.0, -1.0, -1.0};
@@ -297,23 +311,31 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector
         };
         for (int j = 0; j < NY; ++j) {
             for (int i = NX; i < pitch; ++i) cid[((size_t)k * NY + j) * pitch + i] = 0;   // row padding
+            // Away from the outer walls a node's triple is a function of its
+            // eight cells' materials and its PEC bits alone: a node repeating
+            // the previous node's (cells, bits) key takes the previous id.
             const bool inner_row = j >= 1 && j < ny && k >= 1 && k < nz;
             const uint8_t *m00 = inner_row ? mat + (size_t)(k - 1) * sxy + (size_t)(j - 1) * sx : nullptr;
+            bool key_ok = false;
+            uint64_t last_cells = 0;
             for (int i = 0; i < NX; ++i) {
                 const uint8_t pb = pec[((size_t)k * NY + j) * NX + i];
-                if (inner_row && i >= 1 && i < nx && pb == 0) {
+                uint64_t cells = 0;
+                const bool keyed = inner_row && i >= 1 && i < nx;
+                if (keyed) {
                     // cells (i-1..i, j-1..j, k-1..k)
                     const uint8_t *q = m00 + (i - 1);
-                    const uint8_t m = q[0];
-                    if (q[1] == m && q[sx] == m && q[sx + 1] == m && q[sxy] == m && q[sxy + 1] == m &&
-                        q[sxy + sx] == m && q[sxy + sx + 1] == m) {
-                        const float u = ce_uniform[m];
-                        if (u == last.x && u == last.y && u == last.z) {
-                            cid[((size_t)k * NY + j) * pitch + i] = last_id;
-                            continue;
-                        }
+                    cells = (uint64_t)q[0] | (uint64_t)q[1] << 8 | (uint64_t)q[sx] << 16 | (uint64_t)q[sx + 1] << 24 |
+                          (uint64_t)q[sxy] << 32 | (uint64_t)q[sxy + 1] << 40 | (uint64_t)q[sxy + sx] << 48 |
+                          (uint64_t)q[sxy + sx + 1] << 56;
+                    if (key_ok && cells == last_cells && pb == last_pb) {
+                        cid[((size_t)k * NY + j) * pitch + i] = last_id;
+                        continue;
                     }
                 }
+                key_ok = keyed;
+                last_cells = cells;
+                last_pb = pb;
                 const bool wx = (i == 0 && wall[0] == FDTD_WALL_PEC) || (i == nx && wall[1] == FDTD_WALL_PEC);
                 const bool wy = (j == 0 && wall[2] == FDTD_WALL_PEC) || (j == ny && wall[3] == FDTD_WALL_PEC);
                 const bool wz = (k == 0 && wall[4] == FDTD_WALL_PEC) || (k == nz && wall[5] == FDTD_WALL_PEC);
@@ -395,9 +417,9 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector
             remap[k].push_back((uint16_t)t);
         }
     }
-    if (table.size() <= (size_t)kMaxCombo) {
-        ids.c8.reset(new uint8_t[ids.n]);
-        uint8_t *const c8 = ids.c8.get();
+    ids.wide = table.size() > (size_t)kMaxCombo;
+    if (!ids.wide) {
+        uint8_t *const c8 = ids.c8;
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < NZ; ++k) {
             const uint16_t *row = cid + (size_t)k * NY * pitch;
@@ -407,7 +429,6 @@ int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector
                 for (int i = NX; i < pitch; ++i) out[(size_t)j * pitch + i] = 0;
             }
         }
-        ids.cid.reset();
     } else {
 #pragma omp parallel for schedule(static)
         for (int k = 0; k < NZ; ++k) {
@@ -700,7 +721,17 @@ int check_status(fdtd_ctx *c)
 
 int set_geometry(fdtd_ctx *c, const uint8_t *mat)
 {
+    IdScratch &scratch = id_scratch();
+    std::lock_guard<std::mutex> hold(scratch.lock);
     NodeIds ids;
+    ids.n = (size_t)c->h.pitch * (c->g.ny + 1) * (c->g.nz + 1);
+    try {
+        scratch.reserve(ids.n);
+    } catch (const std::bad_alloc &) {
+        return fail(FDTD_ENOMEM, "host scratch for the coefficient ids");
+    }
+    ids.cid = scratch.cid.get();
+    ids.c8 = scratch.c8.get();
     std::vector<float4> table;
     if (int r = build_combo(c, mat, ids, table)) return r;
     c->n_combo = (int)table.size();
@@ -722,9 +753,9 @@ int set_geometry(fdtd_ctx *c, const uint8_t *mat)
         c->plan_dirty = true;
     }
     if (id16)
-        CK(cudaMemcpyAsync((void *)c->h.cid, ids.cid.get(), ids.n * 2, cudaMemcpyHostToDevice, c->cur));
+        CK(cudaMemcpyAsync((void *)c->h.cid, ids.cid, ids.n * 2, cudaMemcpyHostToDevice, c->cur));
     else
-        CK(cudaMemcpyAsync((void *)c->h.cid, ids.c8.get(), ids.n, cudaMemcpyHostToDevice, c->cur));
+        CK(cudaMemcpyAsync((void *)c->h.cid, ids.c8, ids.n, cudaMemcpyHostToDevice, c->cur));
     CK(cudaMemcpyAsync((void *)c->h.ctab, table.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice, c->cur));
     // the host copies stay alive until the copies finish
     CK(cudaStreamSynchronize(c->cur));
