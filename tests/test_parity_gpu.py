@@ -97,6 +97,35 @@ def test_random_grids_fields_match_oracle(fdtd, ncpu, seed, shape, upml):
     s.close()
 
 
+@pytest.mark.parametrize("new_geometry", ["random", "uniform"])
+def test_set_materials_equals_fresh_board(fdtd, ncpu, new_geometry):
+    """fdtd_set_materials on a live board (same eps_r table, PEC and ports):
+    the run that follows equals a board created with the new materials, bit
+    for bit, and the oracle on them.  The random grid has about a thousand
+    distinct edge coefficient triples (16-bit ids), the uniform one a handful
+    (8-bit ids), so the "uniform" case also switches the id width."""
+    a = W.random_problem(21, 31, 23, 17, upml=3, n_steps=60)
+    rng = np.random.default_rng(22)
+    if new_geometry == "random":
+        mat = rng.integers(0, len(a.eps_r), size=a.mat.shape).astype(np.uint8)
+    else:
+        mat = np.full(a.mat.shape, 1, np.uint8)
+    b = a.replace(mat=mat)
+    s = fdtd.Solver(a)
+    s.step(7)                       # the old geometry has run: set_materials also resets
+    s.set_materials(b.mat)
+    s.run()
+    fresh = fdtd.Solver(b)
+    fresh.run()
+    for c in range(6):
+        assert np.array_equal(s.field(c), fresh.field(c)), c
+    assert np.array_equal(s.traces(), fresh.traces())
+    ref = oracle.run(b, n_threads=ncpu, fields=True)
+    _fields_close(s, ref["fields"])
+    s.close()
+    fresh.close()
+
+
 def test_pmc_walls_match_oracle(fdtd, ncpu):
     """PEC top/bottom, PMC side walls (cavity model), anisotropic cells."""
     p = W.box(26, 19, 3, d=(1e-3, 1.3e-3, 0.4e-3), eps_r=4.4, walls=(PMC, PMC, PMC, PMC, PEC, PEC))
