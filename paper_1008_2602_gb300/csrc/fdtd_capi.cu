@@ -964,12 +964,14 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
             // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
             // An auxiliary is needed where D->E (B->H) is graded or both
             // recurrences are; otherwise the lossy form holds exactly.  With
-            // 16-bit field storage every slab component keeps its FP32
-            // auxiliary: the lossy form would apply the per-step UPML decay to
-            // the stored 16-bit value, where decrements below half an ulp are
-            // lost, while the auxiliary recurrence carries them in FP32.
+            // BF16 field storage every slab component keeps its FP32
+            // auxiliary: the lossy form applies the per-step UPML decay to the
+            // stored value, and an 8-bit mantissa loses enough of it to raise
+            // the probe error by half, while the auxiliary recurrence carries
+            // the decay in FP32.  FP16's 11-bit mantissa stays within its
+            // error target with the reduced set.
             const int rec = is_h ? 1 : 0;
-            const bool need = c->prec != FDTD_FP32 || any_nontrivial(w, is_h ? 0 : 1, false, true) ||
+            const bool need = c->prec == FDTD_BF16_STORE || any_nontrivial(w, is_h ? 0 : 1, false, true) ||
                               (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
             sl.aux[comp] = nullptr;
             if (need && !r) {
