@@ -238,6 +238,20 @@ int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls);
  * FDTD_ENOMEM if the scratch cannot grow. */
 int fdtd_set_materials(fdtd_ctx *ctx, const uint8_t *mat_ids);
 
+/* Host only: the per-node edge coefficients fdtd_create builds for a
+ * geometry (arguments as in fdtd_create), without touching a device.  The
+ * coefficient of an E edge is 1/eps_r with eps_r the mean over the cells
+ * sharing the edge; it is 0 on PEC edges and on edges tangential to a PEC
+ * wall.  ids: host [nz+1][ny+1][nx+1] (caller-owned) receives the node's row
+ * in table; table: host [max_rows][4] (caller-owned) receives the distinct
+ * (ce_x, ce_y, ce_z, 0) rows in order of first appearance by plane; *n_rows
+ * their count.  Entries of edges that do not exist (i = nx for x edges, and so
+ * on) are 0.  Errors: as fdtd_create, and FDTD_EINVAL when the table needs
+ * more than max_rows rows (at most 65536). */
+int fdtd_node_coefficients(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat,
+                           const fdtd_box *pec, int n_pec, const uint8_t *pec_mask, const fdtd_boundary *bnd,
+                           uint16_t *ids, float *table, int max_rows, int *n_rows);
+
 /* Fill *info (synchronises to read the step counter). */
 int fdtd_info(fdtd_ctx *ctx, fdtd_info_t *info);
 

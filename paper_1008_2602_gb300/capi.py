@@ -72,6 +72,8 @@ _SIGS = {
     "fdtd_diagnostics": (c_int, [c_void_p, P(c_double), P(c_double)]),
     "fdtd_reset": (c_int, [c_void_p]),
     "fdtd_set_materials": (c_int, [c_void_p, c_void_p]),
+    "fdtd_node_coefficients": (c_int, [P(fdtd_grid), c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
+                                       P(fdtd_boundary), c_void_p, c_void_p, c_int, P(c_int)]),
     "fdtd_info": (c_int, [c_void_p, P(fdtd_info_t)]),
     "fdtd_save": (c_int, [c_void_p, c_void_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
     "fdtd_selftest_wait_timeout": (c_int, [c_void_p, ctypes.c_uint]),

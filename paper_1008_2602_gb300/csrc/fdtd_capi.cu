@@ -802,12 +802,12 @@ const char *fdtd_last_error(void) { return g_err.c_str(); }
 
 void fdtd_destroy(fdtd_ctx *c);
 
-int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat, const fdtd_box *pec,
-                int n_pec, const uint8_t *pec_mask, const fdtd_boundary *bnd, int precision, void *stream,
-                fdtd_ctx **out)
+namespace {
+
+// Argument checks shared by fdtd_create and fdtd_node_coefficients.
+int check_problem(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat, const fdtd_box *pec,
+                  int n_pec, const fdtd_boundary *bnd)
 {
-    if (!out) return fail(FDTD_EINVAL, "out is NULL");
-    *out = nullptr;
     if (!grid || !mat_ids || !eps_r || !bnd) return fail(FDTD_EINVAL, "NULL grid, mat_ids, eps_r or boundary");
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(FDTD_EINVAL, "grid must have at least one cell per axis");
     if (!(grid->dx > 0 && grid->dy > 0 && grid->dz > 0)) return fail(FDTD_EINVAL, "cell sizes must be positive");
@@ -816,7 +816,6 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     for (int m = 0; m < n_mat; ++m)
         if (!(eps_r[m] > 0)) return fail(FDTD_EINVAL, "eps_r must be positive");
     if (n_pec < 0 || (n_pec > 0 && !pec)) return fail(FDTD_EINVAL, "bad PEC box list");
-    if (precision < FDTD_FP32 || precision > FDTD_BF16_STORE) return fail(FDTD_EINVAL, "bad precision");
     const int N[3] = {grid->nx, grid->ny, grid->nz};
     for (int f = 0; f < 6; ++f) {
         if (bnd->depth[f] < 0 || bnd->depth[f] > N[f / 2]) return fail(FDTD_EINVAL, "bad UPML depth");
@@ -829,6 +828,19 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     if (bnd->depth[0] + bnd->depth[1] + bnd->depth[2] + bnd->depth[3] + bnd->depth[4] + bnd->depth[5] > 0 &&
         !(bnd->R0 > 0 && bnd->R0 <= 1 && bnd->m >= 0 && bnd->kappa_max >= 1))
         return fail(FDTD_EINVAL, "UPML needs 0 < R0 <= 1, m >= 0, kappa_max >= 1");
+    return FDTD_OK;
+}
+
+}  // namespace
+
+int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat, const fdtd_box *pec,
+                int n_pec, const uint8_t *pec_mask, const fdtd_boundary *bnd, int precision, void *stream,
+                fdtd_ctx **out)
+{
+    if (!out) return fail(FDTD_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (precision < FDTD_FP32 || precision > FDTD_BF16_STORE) return fail(FDTD_EINVAL, "bad precision");
+    if (int r = check_problem(grid, mat_ids, eps_r, n_mat, pec, n_pec, bnd)) return r;
 
     fdtd_ctx *c = new fdtd_ctx();
     c->g = *grid;
@@ -1471,6 +1483,51 @@ int fdtd_set_materials(fdtd_ctx *c, const uint8_t *mat_ids)
     }
     (void)old;
     return fdtd_reset(c);
+}
+
+int fdtd_node_coefficients(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps_r, int n_mat,
+                           const fdtd_box *pec, int n_pec, const uint8_t *pec_mask, const fdtd_boundary *bnd,
+                           uint16_t *ids, float *table, int max_rows, int *n_rows)
+{
+    if (!ids || !table || !n_rows || max_rows < 1) return fail(FDTD_EINVAL, "NULL output or max_rows < 1");
+    if (int r = check_problem(grid, mat_ids, eps_r, n_mat, pec, n_pec, bnd)) return r;
+    // a host-only context holding what the id precompute reads; no device work
+    fdtd_ctx c;
+    c.g = *grid;
+    c.bnd = *bnd;
+    c.eps.assign(eps_r, eps_r + n_mat);
+    if (n_pec > 0) c.boxes.assign(pec, pec + n_pec);
+    if (pec_mask) c.mask.assign(pec_mask, pec_mask + (size_t)grid->nx * grid->ny * grid->nz);
+    c.h.pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    const int NX = grid->nx + 1, NY = grid->ny + 1, NZ = grid->nz + 1;
+    IdScratch &scratch = id_scratch();
+    std::lock_guard<std::mutex> hold(scratch.lock);
+    NodeIds nid;
+    nid.n = (size_t)c.h.pitch * NY * NZ;
+    try {
+        scratch.reserve(nid.n);
+    } catch (const std::bad_alloc &) {
+        return fail(FDTD_ENOMEM, "host scratch for the coefficient ids");
+    }
+    nid.cid = scratch.cid.get();
+    nid.c8 = scratch.c8.get();
+    std::vector<float4> tab;
+    if (int r = build_combo(&c, mat_ids, nid, tab)) return r;
+    if ((int)tab.size() > max_rows) return fail(FDTD_EINVAL, "more coefficient triples than max_rows");
+    *n_rows = (int)tab.size();
+    for (size_t t = 0; t < tab.size(); ++t) {
+        table[4 * t] = tab[t].x;
+        table[4 * t + 1] = tab[t].y;
+        table[4 * t + 2] = tab[t].z;
+        table[4 * t + 3] = 0.0f;
+    }
+#pragma omp parallel for schedule(static)
+    for (int k = 0; k < NZ; ++k)
+        for (int j = 0; j < NY; ++j) {
+            const size_t src = ((size_t)k * NY + j) * c.h.pitch, dst = ((size_t)k * NY + j) * NX;
+            for (int i = 0; i < NX; ++i) ids[dst + i] = nid.wide ? nid.cid[src + i] : (uint16_t)nid.c8[src + i];
+        }
+    return FDTD_OK;
 }
 
 int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
