@@ -64,17 +64,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(r.stderr)
         return obj
 
-    with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
-        list(ex.map(compile_one, zip(srcs, objs)))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lcudart"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    for o in objs:
-        if os.path.exists(o):
-            os.remove(o)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
+    try:
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
+            list(ex.map(compile_one, zip(srcs, objs)))
+        cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fopenmp", "-o", tmp, *objs, "-lcudart"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stderr}")
+        os.replace(tmp, LIB)
+    finally:   # objects of this build (and a failed link's output) never linger
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 
