@@ -1464,7 +1464,6 @@ int fdtd_set_materials(fdtd_ctx *c, const uint8_t *mat_ids)
 {
     if (!c || !mat_ids) return fail(FDTD_EINVAL, "NULL argument");
     if (c->batch) return fail(FDTD_ESTATE, "context is in a batch");
-    const std::vector<float4> old = c->ctab;
     if (int r = set_geometry(c, mat_ids)) return r;
     // sources keep their edge; refresh their coefficient for the new permittivity
     if (!c->src.empty()) {
@@ -1481,7 +1480,6 @@ int fdtd_set_materials(fdtd_ctx *c, const uint8_t *mat_ids)
             CK(cudaMemcpyAsync((void *)c->h.src, c->src.data(), sizeof(Source) * c->src.size(), cudaMemcpyHostToDevice,
                                c->cur));
     }
-    (void)old;
     return fdtd_reset(c);
 }
 
