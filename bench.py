@@ -449,7 +449,8 @@ def run_reference(args, world, rank):
     n = os.cpu_count() or 1
     oracle.build()
     per = max(1, args.ref_sample_steps)
-    oracle.run(prob, n_steps=1, trace=True, dft=False, n_threads=n)
+    for _ in range(max(1, args.warmup)):   # untimed samples of the same size
+        oracle.run(prob, n_steps=per, trace=True, dft=False, n_threads=n)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
