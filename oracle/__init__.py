@@ -24,7 +24,7 @@ _SRC = os.path.join(_HERE, "fdtd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 
 class _Problem(ctypes.Structure):
@@ -67,10 +67,12 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
 
 
-def _load():
-    global _lib
-    if _lib is None:
-        lib = ctypes.CDLL(build())
+def _load(lib_path: Optional[str] = None):
+    """The oracle library (or, for the tests that plant a mistake in a copy of
+    the oracle, the library built from that copy at ``lib_path``)."""
+    path = lib_path or build()
+    if path not in _libs:
+        lib = ctypes.CDLL(path)
         lib.oracle_run.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_Outputs)]
         lib.oracle_run.restype = ctypes.c_int
         for name in ("oracle_cfl_dt",):
@@ -80,8 +82,8 @@ def _load():
         lib.oracle_cavity_fr.restype = ctypes.c_double
         lib.oracle_pulse.argtypes = [ctypes.c_double] * 4
         lib.oracle_pulse.restype = ctypes.c_double
-        _lib = lib
-    return _lib
+        _libs[path] = lib
+    return _libs[path]
 
 
 def cavity_fr(m: int, n: int, Lx: float, Ly: float, Lz: float, eps_r: float) -> float:
@@ -109,9 +111,10 @@ def n_bins(prob, dt: float) -> int:
 
 def run(prob, *, trace: bool = True, dft: bool = True, energy: bool = False, divb: bool = False,
         src_wave: bool = False, fields: bool = False, vsrc_current: bool = False,
-        n_threads: Optional[int] = None, n_steps: Optional[int] = None) -> dict:
+        n_threads: Optional[int] = None, n_steps: Optional[int] = None,
+        lib_path: Optional[str] = None) -> dict:
     """Run the oracle on a ``workloads.Problem``; returns a dict of numpy arrays."""
-    lib = _load()
+    lib = _load(lib_path)
     N = int(n_steps if n_steps is not None else prob.n_steps)
     mat = np.ascontiguousarray(prob.mat, dtype=np.uint8)
     eps = np.ascontiguousarray(prob.eps_r, dtype=np.float64)
