@@ -46,7 +46,7 @@ typedef enum {
     FDTD_ESTATE = -6      /* call not valid in the context's current state */
 } fdtd_status;
 
-enum { FDTD_FP32 = 0, FDTD_FP16_STORE = 1, FDTD_BF16_STORE = 2 };
+enum { FDTD_FP32 = 0, FDTD_FP16_STORE = 1 };
 enum { FDTD_WALL_PEC = 0, FDTD_WALL_PMC = 1 };
 enum { FDTD_X = 0, FDTD_Y = 1, FDTD_Z = 2 };
 enum { FDTD_EX = 0, FDTD_EY = 1, FDTD_EZ = 2, FDTD_HX = 3, FDTD_HY = 4, FDTD_HZ = 5 };
@@ -110,9 +110,9 @@ typedef struct {
  *  pec_mask  optional host [nz][ny][nx]: nonzero cells are PEC (each acts as a
  *            1x1x1 box); may be NULL.
  *  bnd       UPML depths, grading and outer walls.
- *  precision FDTD_FP32, FDTD_FP16_STORE or FDTD_BF16_STORE (fields stored in
- *            16 bits with a power-of-two scale, arithmetic in FP32; UPML
- *            auxiliary D/B always FP32).
+ *  precision FDTD_FP32, or FDTD_FP16_STORE (fields stored as FP16 with a
+ *            power-of-two scale, arithmetic in FP32; UPML auxiliary D/B
+ *            always FP32).  Any other value is FDTD_EINVAL.
  *  stream    cudaStream_t the context enqueues on; NULL makes the library
  *            create (and later destroy) its own non-blocking stream.
  *  out       receives the context.
@@ -271,25 +271,30 @@ const char *fdtd_last_error(void);
 /* Discrete field energy and max |div B| of fields the caller owns, with no
  * device allocation.  The paper has no counterpart: this is a service for
  * callers that cannot allocate device memory when they need the check --
- * code running while a stream is captured into a CUDA graph, code under a
- * fixed memory budget or pool, real-time loops that forbid allocator calls.
- * It computes the same quantities as fdtd_diagnostics, from raw arrays:
+ * code under a fixed memory budget or pool that must not grow, real-time
+ * loops that forbid allocator calls, hosts that hand the library only
+ * pre-registered buffers.  It computes the same quantities as
+ * fdtd_diagnostics, from raw arrays:
  *  fields   9 device pointers to FP32 [nz+1][ny+1][pitch] arrays (x fastest,
  *           node layout as fdtd_get_field): E^n x,y,z [V/m], H^{n-1/2} x,y,z
  *           and H^{n+1/2} x,y,z [A/m]
  *  eps_r    3 device pointers to the per-edge relative permittivity of the
  *           E_x, E_y, E_z edges in the same layout, or NULL (all 1)
  *  nx,ny,nz cells; pitch >= nx+1 elements; dx,dy,dz cell sizes [m]
- *  upml_depth  6 UPML depths (NULL: none): div B is taken over cells outside
+ *  upml_depth  6 UPML depths (NULL: none), each >= 0 and the two of an axis
+ *           summing to at most its cells (else FDTD_EINVAL): div B is taken
+ *           over the cells outside them
  *  stream   cudaStream_t to run on (NULL: legacy default stream)
- *  energy, max_div_b  host outputs [J] and [T/m] (either may be NULL)
+ *  energy, max_div_b  host outputs [J] and [T/m] (either may be NULL); a NaN
+ *           in H^{n+1/2} inside the window makes max_div_b NaN
  * Scratch space is a fixed static device array that each GPU loading the
  * library holds until exit; grids above 33,554,432 nodes are rejected with
- * FDTD_EINVAL.  The first call on a device resolves the array's device
- * address with that device current, so it must come before any stream
- * capture.  All calls share the array: calls whose work overlaps on the GPU
- * race.  Synchronises the stream; errors as the other calls (message from
- * fdtd_last_error). */
+ * FDTD_EINVAL.  The first call on a device (and the first after a
+ * cudaDeviceReset) resolves the array's device address with that device
+ * current, so it should come before any stream capture.  All calls share the
+ * array: calls whose work overlaps on the GPU race.  The call copies its two
+ * results to host memory and synchronises the stream before returning;
+ * errors as the other calls (message from fdtd_last_error). */
 int fdtd_energy_static(const float *const fields[9], const float *const eps_r[3], int nx, int ny, int nz,
                        int pitch, double dx, double dy, double dz, const int upml_depth[6], void *stream,
                        double *energy, double *max_div_b);

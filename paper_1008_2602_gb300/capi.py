@@ -16,7 +16,7 @@ from . import build as _build
 c_int, c_double, c_void_p, c_longlong = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_longlong
 
 FDTD_OK, FDTD_EINVAL, FDTD_ENOMEM, FDTD_ECUDA, FDTD_EUNSTABLE, FDTD_ETIMEOUT, FDTD_ESTATE = 0, -1, -2, -3, -4, -5, -6
-FDTD_FP32, FDTD_FP16_STORE, FDTD_BF16_STORE = 0, 1, 2
+FDTD_FP32, FDTD_FP16_STORE = 0, 1
 FDTD_WALL_PEC, FDTD_WALL_PMC = 0, 1
 FDTD_X, FDTD_Y, FDTD_Z = 0, 1, 2
 FDTD_EX, FDTD_EY, FDTD_EZ, FDTD_HX, FDTD_HY, FDTD_HZ = range(6)

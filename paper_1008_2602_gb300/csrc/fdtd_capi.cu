@@ -6,7 +6,6 @@
 // step, slab decomposition of the UPML), owns device memory, captures chunks
 // of steps into CUDA graphs and batches boards into one launch per phase.
 #include <nvtx3/nvToolsExt.h>
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -555,8 +554,7 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
     std::vector<CUtensorMap> maps(kNumMaps);
     std::memset(maps.data(), 0, sizeof(CUtensorMap) * kNumMaps);
     const CUtensorMapDataType fdt = c->prec == FDTD_FP32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                  : c->prec == FDTD_FP16_STORE ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
-                                                               : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+                                                         : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const int es = elem_size(c->prec);
     const uint64_t d0 = h.pitch, d1 = h.ny + 1, d2 = h.nz + 1;
     for (int par = 0; par < 2; ++par)
@@ -612,6 +610,12 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
                Plan &plan, cudaStream_t st, std::vector<long long> &host)
 {
     const int nb = (int)boards.size();
+    for (int b = 0; b < nb; ++b)
+        if (!fused_maps_match(boards[b]->h, t.tile_x, t.tile_y))
+            return fail(FDTD_EINVAL, "fused tile " + std::to_string(t.tile_x) + "x" + std::to_string(t.tile_y) +
+                                         " does not match the board's tensor maps (" +
+                                         std::to_string(boards[b]->h.tm_tx) + "x" + std::to_string(boards[b]->h.tm_ty) +
+                                         "); nothing was launched");
     long long n_slab_blk = 0;
     for (int b = 0; b < nb; ++b) n_slab_blk += boards[b]->h.slab_blocks;
     static_assert(sizeof(SlabBlock) == 4 * sizeof(long long), "slab block descriptor layout");
@@ -714,6 +718,8 @@ int check_status(fdtd_ctx *c)
 {
     int st = 0;
     CK(cudaMemcpy(&st, c->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & 4) return fail(FDTD_EINVAL, "a fused-kernel launch did not match the board's tensor maps; its items were "
+                                         "skipped (results of this run are invalid)");
     if (st & 2) return fail(FDTD_ETIMEOUT, "a fused-kernel TMA wait gave up (results of this run are invalid)");
     if (st & 1) return fail(FDTD_EUNSTABLE, "non-finite probe sample (unstable run: check the Courant number)");
     return FDTD_OK;
@@ -839,7 +845,8 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
 {
     if (!out) return fail(FDTD_EINVAL, "out is NULL");
     *out = nullptr;
-    if (precision < FDTD_FP32 || precision > FDTD_BF16_STORE) return fail(FDTD_EINVAL, "bad precision");
+    if (precision != FDTD_FP32 && precision != FDTD_FP16_STORE)
+        return fail(FDTD_EINVAL, "precision must be FDTD_FP32 or FDTD_FP16_STORE");
     if (int r = check_problem(grid, mat_ids, eps_r, n_mat, pec, n_pec, bnd)) return r;
 
     fdtd_ctx *c = new fdtd_ctx();
@@ -975,15 +982,12 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
             // E: D recurrence along w1, E recurrence along w2 (integer), D->E along w (half)
             // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
             // An auxiliary is needed where D->E (B->H) is graded or both
-            // recurrences are; otherwise the lossy form holds exactly.  With
-            // BF16 field storage every slab component keeps its FP32
-            // auxiliary: the lossy form applies the per-step UPML decay to the
-            // stored value, and an 8-bit mantissa loses enough of it to raise
-            // the probe error by half, while the auxiliary recurrence carries
-            // the decay in FP32.  FP16's 11-bit mantissa stays within its
-            // error target with the reduced set.
+            // recurrences are; otherwise the lossy form holds exactly (also
+            // with FP16 field storage, whose 11-bit mantissa keeps the
+            // per-step UPML decay applied to the stored value within the
+            // storage mode's error target).
             const int rec = is_h ? 1 : 0;
-            const bool need = c->prec == FDTD_BF16_STORE || any_nontrivial(w, is_h ? 0 : 1, false, true) ||
+            const bool need = any_nontrivial(w, is_h ? 0 : 1, false, true) ||
                               (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
             sl.aux[comp] = nullptr;
             if (need && !r) {
@@ -1262,8 +1266,7 @@ int fdtd_get_field(fdtd_ctx *c, int field, float *out)
                 const size_t src = ((size_t)k * NY + j) * h.pitch + i;
                 float v;
                 if (c->prec == FDTD_FP32) v = ((const float *)buf.data())[src];
-                else if (c->prec == FDTD_FP16_STORE) v = __half2float(((const __half *)buf.data())[src]);
-                else v = __bfloat162float(((const __nv_bfloat16 *)buf.data())[src]);
+                else v = __half2float(((const __half *)buf.data())[src]);
                 out[((size_t)k * NY + j) * NX + i] = (float)(v * s);
             }
     return FDTD_OK;
@@ -1286,8 +1289,7 @@ int fdtd_get_plane(fdtd_ctx *c, int field, int k, float *out)
     for (size_t t = 0; t < (size_t)NX * NY; ++t) {
         float v;
         if (c->prec == FDTD_FP32) v = ((const float *)buf.data())[t];
-        else if (c->prec == FDTD_FP16_STORE) v = __half2float(((const __half *)buf.data())[t]);
-        else v = __bfloat162float(((const __nv_bfloat16 *)buf.data())[t]);
+        else v = __half2float(((const __half *)buf.data())[t]);
         out[t] = (float)(v * s);
     }
     return FDTD_OK;

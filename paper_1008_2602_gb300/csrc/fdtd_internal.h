@@ -52,7 +52,7 @@ constexpr int kPitchAlign = 64;
 constexpr int kMaxCombo = 256;
 constexpr int kMaxCombo16 = 65536;
 
-enum Prec : int { kFP32 = 0, kFP16 = 1, kBF16 = 2 };
+enum Prec : int { kFP32 = 0, kFP16 = 1 };
 
 // Per-position UPML factors (b1, g, ap, am).
 struct Coef {
@@ -132,7 +132,8 @@ struct Board {
     int n_bins;
     double *dft;                  // [n_probe][n_bins][2]
     long long *dft_done;          // samples already folded into dft
-    int *status;                  // bit 0: non-finite probe sample seen
+    int *status;                  // bit 0: non-finite probe sample seen; bit 1: a bounded wait
+                                  // gave up; bit 2: tile / tensor-map mismatch (item skipped)
     int pad1;
 };
 
@@ -174,6 +175,17 @@ __host__ __device__ constexpr int box_h(int tx) { return box_up(tx + 8, 8); }
 __host__ __device__ constexpr int box_c8(int tx) { return box_up(tx + 15, 16); }
 __host__ __device__ constexpr int box_c16(int tx) { return box_up(tx + 7, 8); }
 __host__ __device__ constexpr int box_a(int tx) { return box_up(tx + 5, 4); }
+
+// The fused kernel instantiated for tile_x x tile_y columns stages TMA boxes
+// whose sizes are baked into the board's tensor maps (tm_tx x tm_ty).  A
+// kernel whose tile differs from the maps' would copy boxes past its shared
+// memory stage, so every plan build checks the agreement on the host (no
+// device work), and the kernels re-check it per work item (status bit 4).
+inline bool fused_maps_match(const Board &h, int tile_x, int tile_y)
+{
+    if (h.ix1 <= h.ix0 || h.iy1 <= h.iy0) return true;   // no fused region: no maps are used
+    return h.tm != nullptr && h.tm_tx == tile_x && h.tm_ty == tile_y;
+}
 
 constexpr int kSlabThreads = 256;
 constexpr int kSlabKz = 8;          // planes per slab-kernel thread

@@ -19,7 +19,6 @@
 // All curl and update arithmetic goes through curl2()/the update helpers (or
 // their paired FFMA2 forms) with explicit round-to-nearest intrinsics, so a
 // value recomputed as a halo is bit-identical to the one its owner stores.
-#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include "fdtd_internal.h"
@@ -40,12 +39,6 @@ struct Io<__half> {
     static __device__ __forceinline__ float ld(const __half *p) { return __half2float(__ldg(p)); }
     static __device__ __forceinline__ float ldw(const __half *p) { return __half2float(*p); }
     static __device__ __forceinline__ void st(__half *p, float v) { *p = __float2half_rn(v); }
-};
-template <>
-struct Io<__nv_bfloat16> {
-    static __device__ __forceinline__ float ld(const __nv_bfloat16 *p) { return __bfloat162float(__ldg(p)); }
-    static __device__ __forceinline__ float ldw(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float v) { *p = __float2bfloat16_rn(v); }
 };
 
 // ------------------------------------------------------------------ arithmetic
@@ -215,8 +208,6 @@ template <>
 __device__ __forceinline__ float cvt<float>(float v) { return v; }
 template <>
 __device__ __forceinline__ float cvt<__half>(__half v) { return __half2float(v); }
-template <>
-__device__ __forceinline__ float cvt<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
 
 // Two adjacent elements of one row (8-byte aligned for FP32, 4-byte for the
 // 16-bit storage types), converted to/from FP32.
@@ -240,21 +231,6 @@ struct Pair<__half> {
     }
     static __device__ __forceinline__ void st(__half *p, float2 v) { *reinterpret_cast<__half2 *>(p) = __float22half2_rn(v); }
 };
-template <>
-struct Pair<__nv_bfloat16> {
-    static __device__ __forceinline__ float2 lds(const __nv_bfloat16 *p)
-    {
-        return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
-    }
-    static __device__ __forceinline__ float2 ldg(const __nv_bfloat16 *p)
-    {
-        return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162 *>(p)));
-    }
-    static __device__ __forceinline__ void st(__nv_bfloat16 *p, float2 v)
-    {
-        *reinterpret_cast<__nv_bfloat162 *>(p) = __float22bfloat162_rn(v);
-    }
-};
 
 // Stores of the fused kernel.  Written as global-space stores without a
 // compiler memory barrier, so the compiler knows they cannot alias the
@@ -270,11 +246,6 @@ __device__ __forceinline__ void stg1(__half *p, float v)
     const __half h = __float2half_rn(v);
     asm volatile("st.global.b16 [%0], %1;" ::"l"(gaddr(p)), "h"(*reinterpret_cast<const unsigned short *>(&h)));
 }
-__device__ __forceinline__ void stg1(__nv_bfloat16 *p, float v)
-{
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    asm volatile("st.global.b16 [%0], %1;" ::"l"(gaddr(p)), "h"(*reinterpret_cast<const unsigned short *>(&h)));
-}
 __device__ __forceinline__ void stg2(float *p, float2 v)
 {
     asm volatile("st.global.v2.f32 [%0], {%1, %2};" ::"l"(gaddr(p)), "f"(v.x), "f"(v.y));
@@ -282,11 +253,6 @@ __device__ __forceinline__ void stg2(float *p, float2 v)
 __device__ __forceinline__ void stg2(__half *p, float2 v)
 {
     const __half2 h = __float22half2_rn(v);
-    asm volatile("st.global.b32 [%0], %1;" ::"l"(gaddr(p)), "r"(*reinterpret_cast<const unsigned int *>(&h)));
-}
-__device__ __forceinline__ void stg2(__nv_bfloat16 *p, float2 v)
-{
-    const __nv_bfloat162 h = __float22bfloat162_rn(v);
     asm volatile("st.global.b32 [%0], %1;" ::"l"(gaddr(p)), "r"(*reinterpret_cast<const unsigned int *>(&h)));
 }
 
@@ -375,7 +341,9 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
     const long long *prefix = ZP ? plan.zp_prefix : plan.int_prefix;
     const int b = find_board(prefix, plan.nb, item);
     t.B = plan.boards[b];
-    t.ok = active_ro(t.B);
+    // a board whose tensor maps were encoded for another tile is skipped (its
+    // boxes would not fit this kernel's stages); the producer flags it
+    t.ok = active_ro(t.B) && t.B->tm_tx == kWarpCols * W && t.B->tm_ty == TY;
     const long long step = step_ro(t.B);
     t.par = (int)(step & 1);
     const long long local = item - __ldg(prefix + b);
@@ -468,6 +436,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
             if (item >= n_items) break;
             const Tile t = decode_tile<TY, W, ZP>(plan, item);
             const Board *B = t.B;
+            if (!t.ok && (B->tm_tx != kWarpCols * W || B->tm_ty != TY)) atomicOr(B->status, 4);
             const CUtensorMap *tm = B->tm;
             const int id16 = B->id16;
             const int xe0 = (t.i0 - 1) & ~7;
@@ -864,18 +833,6 @@ struct Word<__half> {
     {
         const unsigned b = __float_as_uint(w);
         return __half2float(__ushort_as_half((unsigned short)((e & 1) ? b >> 16 : b & 0xffffu)));
-    }
-};
-template <>
-struct Word<__nv_bfloat16> {
-    static __device__ __forceinline__ const void *at(const __nv_bfloat16 *p)
-    {
-        return (const void *)((uintptr_t)p & ~(uintptr_t)3);
-    }
-    static __device__ __forceinline__ float get(float w, long long e)
-    {
-        const unsigned b = __float_as_uint(w);
-        return __uint_as_float((e & 1) ? (b & 0xffff0000u) : (b << 16));
     }
 };
 
@@ -1447,7 +1404,6 @@ cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cu
 {
     switch (prec) {
     case kFP16: return phase_t<__half>(plan, phase, grid_cap, st);
-    case kBF16: return phase_t<__nv_bfloat16>(plan, phase, grid_cap, st);
     default: return phase_t<float>(plan, phase, grid_cap, st);
     }
 }
@@ -1479,8 +1435,8 @@ static cudaError_t limits_t()
 
 cudaError_t fused_set_smem_limits()
 {
-    cudaError_t a = limits_t<float>(), b = limits_t<__half>(), c = limits_t<__nv_bfloat16>();
-    return a != cudaSuccess ? a : (b != cudaSuccess ? b : c);
+    cudaError_t a = limits_t<float>(), b = limits_t<__half>();
+    return a != cudaSuccess ? a : b;
 }
 
 cudaError_t launch_dft(const Plan &plan, int grid_cap, cudaStream_t st)
@@ -1512,7 +1468,6 @@ cudaError_t launch_energy(const Board *b_dev, const Board &b_host, double *parti
 {
     switch (b_host.prec) {
     case kFP16: k_energy<__half><<<n_part, 256, 0, st>>>(b_dev, partials); break;
-    case kBF16: k_energy<__nv_bfloat16><<<n_part, 256, 0, st>>>(b_dev, partials); break;
     default: k_energy<float><<<n_part, 256, 0, st>>>(b_dev, partials); break;
     }
     k_energy_final<<<1, 256, 0, st>>>(partials, n_part, out2);

@@ -2,22 +2,25 @@
 // |div B| of caller-owned fields, computed without allocating anything.
 //
 // Why it exists: some callers cannot allocate device memory at the point
-// where they need this check -- code running while a stream is being
-// captured into a CUDA graph, code under a memory pool or budget that must
+// where they need this check -- code under a memory pool or budget that must
 // not grow, real-time loops that forbid allocator calls, or hosts that hand
 // the library only pre-registered buffers.  They pass their fields as device
 // pointers and get the two numbers back, and this call performs no
-// cudaMalloc, cudaFree or other allocation.
+// cudaMalloc, cudaFree or other allocation.  It reads the two results back
+// into host memory and synchronises the stream before it returns.
 //
 // The per-block partial sums live in a file-scope static __device__ array of
 // a fixed size, which every GPU that loads the library holds until the
 // process exits.  Host code may only use the array's device address obtained
 // from cudaGetSymbolAddress (the symbol itself is a host-side stand-in): the
 // first call on each device looks it up with that device current and caches
-// it, so that first call must not happen while a stream is being captured.
-// All calls share the array: two calls whose kernels overlap on the GPU race
-// and both results are then undefined.  Every call overwrites each partial it
-// reads, so nothing carries over from the previous call.
+// it, so that first call should come before any stream capture.  The cache is
+// keyed on the device's current CUDA context as well, so a call after
+// cudaDeviceReset (a new primary context, with the array at a possibly new
+// address) looks the address up again.  All calls share the array: two calls
+// whose kernels overlap on the GPU race and both results are then undefined.
+// Every call overwrites each partial it reads, so nothing carries over from
+// the previous call.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -38,7 +41,11 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) double g_energy_scratch[3 * kStaticBlocks + 3];
 
 std::mutex g_mu;
-double *g_scratch_dev[kMaxDevices] = {nullptr};   // device address of the array, per device ordinal
+struct ScratchAddr {
+    CUcontext ctx = nullptr;      // context the address was resolved in
+    double *ptr = nullptr;        // device address of the array there
+};
+ScratchAddr g_scratch_dev[kMaxDevices];   // per device ordinal
 
 struct StaticArgs {
     const float *f[9];      // E^n (x,y,z), H^{n-1/2} (x,y,z), H^{n+1/2} (x,y,z)
@@ -47,6 +54,10 @@ struct StaticArgs {
     int cx0, cx1, cy0, cy1, cz0, cz1;   // cells outside the UPML
     double ix, iy, iz;      // 1/dx, 1/dy, 1/dz
 };
+
+// max that keeps a NaN (fmax would drop it), so a field that has blown up
+// shows in max |div B| as well as in the energy
+__device__ __forceinline__ double nan_max(double a, double b) { return (a != a || b != b) ? NAN : fmax(a, b); }
 
 // One block reduces nodes [b * kNodesPerBlock, (b + 1) * kNodesPerBlock):
 // sum of dual-weighted eps_r E.E and H.H' and max |div H'| over cells
@@ -77,7 +88,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_energy_static(StaticArgs a, 
         if (i >= a.cx0 && i < a.cx1 && j >= a.cy0 && j < a.cy1 && k >= a.cz0 && k < a.cz1) {
             const double dv = ((double)a.f[6][q + 1] - a.f[6][q]) * a.ix + ((double)a.f[7][q + X] - a.f[7][q]) * a.iy +
                               ((double)a.f[8][q + P] - a.f[8][q]) * a.iz;
-            dmax = fmax(dmax, fabs(dv));
+            dmax = nan_max(dmax, fabs(dv));
         }
     }
     __shared__ double se[kStaticThreads], sh[kStaticThreads], sd[kStaticThreads];
@@ -89,7 +100,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_energy_static(StaticArgs a, 
         if ((int)threadIdx.x < off) {
             se[threadIdx.x] += se[threadIdx.x + off];
             sh[threadIdx.x] += sh[threadIdx.x + off];
-            sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + off]);
+            sd[threadIdx.x] = nan_max(sd[threadIdx.x], sd[threadIdx.x + off]);
         }
         __syncthreads();
     }
@@ -107,7 +118,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_energy_static_final(double *
     for (int t = threadIdx.x; t < nblk; t += blockDim.x) {
         a += scratch[3 * t];
         b += scratch[3 * t + 1];
-        m = fmax(m, scratch[3 * t + 2]);
+        m = nan_max(m, scratch[3 * t + 2]);
     }
     se[threadIdx.x] = a;
     sh[threadIdx.x] = b;
@@ -117,7 +128,7 @@ __global__ void __launch_bounds__(kStaticThreads) k_energy_static_final(double *
         if ((int)threadIdx.x < off) {
             se[threadIdx.x] += se[threadIdx.x + off];
             sh[threadIdx.x] += sh[threadIdx.x + off];
-            sd[threadIdx.x] = fmax(sd[threadIdx.x], sd[threadIdx.x + off]);
+            sd[threadIdx.x] = nan_max(sd[threadIdx.x], sd[threadIdx.x + off]);
         }
         __syncthreads();
     }
@@ -130,8 +141,27 @@ __global__ void __launch_bounds__(kStaticThreads) k_energy_static_final(double *
 
 int static_fail(int code, const std::string &m) { return fdtd::set_error(code, m.c_str()); }
 
-// Device address of the static array on the current device (looked up once
-// per device, with that device current).
+// cuCtxGetCurrent from the driver, through the runtime's entry-point query
+// (the library links only the runtime).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+CtxGetCurrentFn ctx_getter()
+{
+    static CtxGetCurrentFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrentFn)p;
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// Device address of the static array on the current device, looked up with
+// that device current once per (device, context).
 int scratch_address(double **out)
 {
     int dev = 0;
@@ -139,14 +169,22 @@ int scratch_address(double **out)
     if (e != cudaSuccess) return static_fail(FDTD_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return static_fail(FDTD_EINVAL, "device ordinal beyond the supported range");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_dev[dev]) {
+    CtxGetCurrentFn get_ctx = ctx_getter();
+    if (!get_ctx) return static_fail(FDTD_ECUDA, "cuCtxGetCurrent is not available from the driver");
+    CUcontext ctx = nullptr;
+    if (get_ctx(&ctx) != CUDA_SUCCESS) ctx = nullptr;
+    ScratchAddr &slot = g_scratch_dev[dev];
+    if (!ctx || !slot.ptr || slot.ctx != ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_energy_scratch);
+        e = cudaGetSymbolAddress(&p, g_energy_scratch);   // makes the device's primary context current if none is
         if (e != cudaSuccess || !p)
             return static_fail(FDTD_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-        g_scratch_dev[dev] = static_cast<double *>(p);
+        if (get_ctx(&ctx) != CUDA_SUCCESS || !ctx)
+            return static_fail(FDTD_ECUDA, "no current CUDA context after cudaGetSymbolAddress");
+        slot.ctx = ctx;
+        slot.ptr = static_cast<double *>(p);
     }
-    *out = g_scratch_dev[dev];
+    *out = slot.ptr;
     return FDTD_OK;
 }
 
@@ -161,6 +199,15 @@ extern "C" int fdtd_energy_static(const float *const fields[9], const float *con
         if (!fields[t]) return static_fail(FDTD_EINVAL, "a field pointer is NULL");
     if (nx < 1 || ny < 1 || nz < 1 || pitch < nx + 1) return static_fail(FDTD_EINVAL, "bad grid size or pitch");
     if (!(dx > 0 && dy > 0 && dz > 0)) return static_fail(FDTD_EINVAL, "cell sizes must be positive");
+    if (upml_depth) {
+        // the div B window [d_lo, n - d_hi) reads one node past its last cell
+        // along each axis, which stays inside the caller's arrays only for
+        // depths that are >= 0 and do not overlap
+        const int n3[3] = {nx, ny, nz};
+        for (int w = 0; w < 3; ++w)
+            if (upml_depth[2 * w] < 0 || upml_depth[2 * w + 1] < 0 || upml_depth[2 * w] + upml_depth[2 * w + 1] > n3[w])
+                return static_fail(FDTD_EINVAL, "UPML depths must be >= 0 and the two depths of an axis at most its cells");
+    }
     const long long total = (long long)(nx + 1) * (ny + 1) * (nz + 1);
     const long long nblk = (total + kNodesPerBlock - 1) / kNodesPerBlock;
     if (nblk > kStaticBlocks)

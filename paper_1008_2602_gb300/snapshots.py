@@ -47,7 +47,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--out", default="snapshots")
     ap.add_argument("--steps", type=int, nargs="+", default=[100, 200, 300, 400, 600, 800])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     a = ap.parse_args(argv)
     snaps = ez_snapshots(W.fig3_board(), a.steps, precision=a.precision)
     os.makedirs(a.out, exist_ok=True)

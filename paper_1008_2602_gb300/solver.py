@@ -15,7 +15,7 @@ import numpy as np
 
 from . import capi as C
 
-PRECISION = {"fp32": C.FDTD_FP32, "fp16": C.FDTD_FP16_STORE, "bf16": C.FDTD_BF16_STORE}
+PRECISION = {"fp32": C.FDTD_FP32, "fp16": C.FDTD_FP16_STORE}
 
 
 def _stream_ptr(stream) -> Optional[int]:

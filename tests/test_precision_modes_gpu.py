@@ -1,16 +1,13 @@
-"""FP16 / BF16 field storage (FP32 arithmetic) on the quarter-scale copy of
+"""FP16 field storage (FP32 arithmetic) on the quarter-scale copy of
 the 880x680x100 multilayer board (280x230x100, 1000 steps with the pulse
 moved early so the run carries a full pulse), against the FP32 run and
 against the FP64 oracle:
 
 * probe traces: relative L2 over all probes, FP32 <= 1e-4 of the oracle,
-  FP16 <= 1e-2 (the target for reduced storage); BF16, whose 8-bit mantissa
-  drops per-step increments below half an ulp, is held to the 6e-2 it
-  reaches on the small PCB;
+  FP16 <= 1e-2 (the target for reduced storage);
 * FP32 and FP16: the spectral peak of every probe with signal stays within
   one running-DFT bin of the oracle's (1000 steps give coarse bins, where a
-  broad peak can sit between two nearly equal bins).  BF16 is not held to
-  this: its peak on a broad, short-run spectrum can move by a few bins.
+  broad peak can sit between two nearly equal bins).
 """
 import numpy as np
 import pytest
@@ -20,7 +17,7 @@ from paper_1008_2602_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-4, "fp16": 1e-2, "bf16": 6e-2}
+TOL = {"fp32": 1e-4, "fp16": 1e-2}
 
 
 @pytest.fixture(scope="module")
@@ -40,7 +37,7 @@ def quarter():
 def runs(quarter, ncpu):
     from paper_1008_2602_gb300 import solver
     out = {"oracle": oracle.run(quarter, n_threads=ncpu)}
-    for prec in ("fp32", "fp16", "bf16"):
+    for prec in ("fp32", "fp16"):
         s = solver.Solver(quarter, precision=prec)
         s.run()
         out[prec] = {"trace": s.traces().astype(np.float64), "spectra": s.spectra()}
@@ -52,7 +49,7 @@ def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp16", "bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "fp16"])
 def test_storage_mode_error(runs, prec):
     ref = runs["oracle"]
     got = runs[prec]
@@ -62,8 +59,6 @@ def test_storage_mode_error(runs, prec):
     e_fp32 = rel_l2(got["trace"][live], runs["fp32"]["trace"][live])
     assert e_oracle <= TOL[prec], (prec, e_oracle, e_fp32)
     assert e_fp32 <= TOL[prec] + 1e-4
-    if prec == "bf16":
-        return
     for q in np.nonzero(live)[0]:
         shift = np.argmax(np.abs(got["spectra"][q][1:])) - np.argmax(np.abs(ref["spectra"][q][1:]))
         assert abs(int(shift)) <= 1, (q, shift)

@@ -1,7 +1,8 @@
 """Table 1 of the paper reproduced on the GPU (Results section): the
 40 x 30 x 0.8 mm board driven by the resistive voltage source (V0 = 5 V,
 Rs = 10 ohm) at one corner, E_z probed at the opposite corner, 30000 steps
-of 1 ps.  The FP32 trace follows the FP64 oracle's, and the lowest isolated
+of 1 ps.  The FP32 trace matches the FP64 oracle's to the FP32 relative-L2
+target of 1e-4, and the lowest isolated
 resonances land in the band of the paper's own modelled peaks around Eq. 9's
 predictions (tests/golden/table1_resonances.txt)."""
 import os
@@ -47,7 +48,7 @@ def test_table1_reproduction_on_gpu(ncpu):
     dt = s.dt
     s.close()
     ref = oracle.run(p, dft=False, n_threads=ncpu)["trace"][0]
-    assert np.linalg.norm(x - ref) <= 1e-3 * np.linalg.norm(ref)
+    assert np.linalg.norm(x - ref) <= 1e-4 * np.linalg.norm(ref)   # the FP32 target
     peaks = _peaks(x, dt)
     rows = {(m, n): pred * 1e9 for m, n, pred, _, _ in _table1()}
     for mode in [(1, 0), (0, 1), (2, 0), (0, 2), (3, 0)]:

@@ -1,13 +1,20 @@
 """fdtd_energy_static: the energy / div B check for callers that cannot
-allocate device memory (e.g. while capturing a CUDA graph or under a fixed
-memory budget).  It works on caller-owned device buffers and keeps its
-scratch in a fixed static device array, so it must agree with the context's
-fdtd_diagnostics (which uses scratch allocated at fdtd_create) -- here on
-two calls in a row, on two different field states, so that a call cannot
-lean on what the previous one left in the shared array.
+allocate device memory (code under a fixed memory budget or pool, real-time
+loops that forbid allocator calls).  It works on caller-owned device buffers
+and keeps its scratch in a fixed static device array, so it must agree with
+the context's fdtd_diagnostics (which uses scratch allocated at fdtd_create)
+-- here on two calls in a row, on two different field states, so that a call
+cannot lean on what the previous one left in the shared array; once on a
+board without UPML whose buffers are unpadded (pitch = nx + 1), once on a
+board with a different UPML depth on every face whose buffers carry row
+padding (pitch = nx + 8), where the div B window and the padded indexing are
+what differ from the context's own kernel.
 
-This file is collected last on purpose: if it fails, a run that stops at the
-first failure has already run every other test.
+The argument checks (grid size limit, UPML depths) come before any device
+work, so those tests run on the CPU.
+
+This file is collected last on purpose: if its GPU test fails, a run that
+stops at the first failure has already run every other test.
 """
 import ctypes
 
@@ -15,8 +22,6 @@ import numpy as np
 import pytest
 
 from paper_1008_2602_gb300 import workloads as W
-
-pytestmark = pytest.mark.gpu
 
 MU0 = 4e-7 * np.pi
 
@@ -33,30 +38,40 @@ def _state(s, steps_before):
     return e + h0 + h1, energy, divb
 
 
-def test_energy_static_matches_context_diagnostics_twice():
+def _padded(a, pitch):
+    """[nz+1][ny+1][nx+1] host array -> [nz+1][ny+1][pitch] with zero padding."""
+    out = np.zeros(a.shape[:2] + (pitch,), np.float32)
+    out[..., : a.shape[2]] = a
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("upml,pad", [((0,) * 6, 0), ((2, 3, 1, 4, 3, 2), 7)])
+def test_energy_static_matches_context_diagnostics_twice(upml, pad):
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.fail("a CUDA device is required for -m gpu tests")
     from paper_1008_2602_gb300 import capi, solver
 
     eps_r = 2.5
-    p = W.box(30, 22, 14, d=(1e-3, 1.2e-3, 0.7e-3), eps_r=eps_r)
+    p = W.box(30, 22, 14, d=(1e-3, 1.2e-3, 0.7e-3), eps_r=eps_r, upml=upml)
     p = W.add_ports(p, [(12, 9, 6, 2), (20, 14, 4, 0)], [(12, 9, 6, 2)], n_steps=400)
+    pitch = p.nx + 1 + pad
     s = solver.Solver(p)
     dev = torch.device("cuda", torch.cuda.current_device())
-    eps = torch.full((p.nz + 1, p.ny + 1, p.nx + 1), eps_r, dtype=torch.float32, device=dev)
+    eps = torch.full((p.nz + 1, p.ny + 1, pitch), eps_r, dtype=torch.float32, device=dev)
     eps_ptrs = (ctypes.c_void_p * 3)(*([eps.data_ptr()] * 3))
-    depth = (ctypes.c_int * 6)(*([0] * 6))
+    depth = (ctypes.c_int * 6)(*upml)
     stream = torch.cuda.current_stream()
 
     # two states, each checked right after the other on the shared scratch
     states = [_state(s, 150), _state(s, 120)]
     results = []
     for fields, _, _ in states:
-        bufs = [torch.from_numpy(np.ascontiguousarray(f)).to(dev) for f in fields]
+        bufs = [torch.from_numpy(_padded(f, pitch)).to(dev) for f in fields]
         ptrs = (ctypes.c_void_p * 9)(*[b.data_ptr() for b in bufs])
         energy, divb = ctypes.c_double(), ctypes.c_double()
-        capi.fdtd_energy_static(ptrs, eps_ptrs, p.nx, p.ny, p.nz, p.nx + 1, p.dx, p.dy, p.dz, depth,
+        capi.fdtd_energy_static(ptrs, eps_ptrs, p.nx, p.ny, p.nz, pitch, p.dx, p.dy, p.dz, depth,
                                 ctypes.c_void_p(stream.cuda_stream), ctypes.byref(energy), ctypes.byref(divb))
         results.append((energy.value, divb.value, max(np.abs(f).max() for f in fields[6:])))
         del bufs
@@ -70,11 +85,21 @@ def test_energy_static_matches_context_diagnostics_twice():
     s.close()
 
 
-def test_energy_static_rejects_oversized_grids():
-    pytest.importorskip("torch")
-    from paper_1008_2602_gb300 import capi
-    ptrs = (ctypes.c_void_p * 9)(*([1] * 9))   # never dereferenced: the size check comes first
+def _call(capi, nx, ny, nz, pitch, depth):
+    ptrs = (ctypes.c_void_p * 9)(*([1] * 9))   # never dereferenced: the argument checks come first
+    d = (ctypes.c_int * 6)(*depth) if depth is not None else None
     with pytest.raises(capi.FdtdError) as ei:
-        capi.fdtd_energy_static(ptrs, None, 1000, 1000, 100, 1001, 1e-3, 1e-3, 1e-3, None, None, None, None)
+        capi.fdtd_energy_static(ptrs, None, nx, ny, nz, pitch, 1e-3, 1e-3, 1e-3, d, None, None, None)
     assert ei.value.code == capi.FDTD_EINVAL
-    assert "at most" in capi.lib.fdtd_last_error().decode()
+    return capi.lib.fdtd_last_error().decode()
+
+
+def test_energy_static_rejects_oversized_grids():
+    from paper_1008_2602_gb300 import capi
+    assert "at most" in _call(capi, 1000, 1000, 100, 1001, None)
+
+
+@pytest.mark.parametrize("depth", [(-1, 0, 0, 0, 0, 0), (0, 0, 0, -3, 0, 0), (6, 5, 0, 0, 0, 0), (0, 0, 0, 0, 9, 2)])
+def test_energy_static_rejects_bad_upml_depths(depth):
+    from paper_1008_2602_gb300 import capi
+    assert "UPML" in _call(capi, 10, 12, 10, 11, depth)
