@@ -488,7 +488,7 @@ def main():
     ap.add_argument("--plain-requests", type=int, default=16)
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--window", type=int, default=200)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--tile-x", type=int, default=0, help="fused tile width (62 or 124 columns); 0 = tuned default")
     ap.add_argument("--tile-y", type=int, default=0, help="fused tile height (4 or 8 rows); 0 = tuned default")
     ap.add_argument("--zseg", type=int, default=0, help="fused z-segment length; 0 = tuned default")
