@@ -19,8 +19,16 @@ roofline: the fused interior launch (the dominant kernel), algorithmic
          bandwidth; the z-UPML launch (+16 B of auxiliaries per node) is
          reported beside it.
 cpu_baseline: the FP64 oracle on the same full-size grid for a few steps.
+batched: the batched half of the metric, measured in the same run: 64 uneven
+         boards x 5000 steps in one batch (one timed batched solve) against the
+         same 64 boards solved one at a time (solves/s of each, their ratio,
+         the largest trace difference, clocks).
+served / served_fp16: a short Poisson stream (24 requests at 20 req/s,
+         boards and steps scaled by 1/4) served by continuous batching
+         (solves/s, p50/p99 latency) against the same requests served one at
+         a time, in FP32 and FP16 storage.
 
-Other workloads: --workload small | realistic | batched | served.
+Other workloads: --workload small | realistic | batched | served (full lines).
 """
 from __future__ import annotations
 
@@ -316,31 +324,33 @@ def _plain_solves(probs, precision, tuning=None):
     return time.perf_counter() - t0, out
 
 
-def run_batched(args, world, rank, local):
+def batched_record(boards, batch_steps, precision, window, steps, warmup, world, rank, local, plain_boards):
     """64 uneven boards (plane sides 20-120 mm, 1-3 pairs, dx=0.5 mm,
-    5000 steps each) in one batch; a bench step is one full batched solve."""
+    5000 steps each) in one batch; a step is one full batched solve.  The
+    same boards (the first `plain_boards` of them) are then solved one at a
+    time with per-board launches, and the traces compared."""
     import numpy as np
     import torch
     from paper_1008_2602_gb300 import solver, tune, workloads as W
     torch.cuda.set_device(local)
-    probs = W.batch_boards(seed=4 + 100 * rank, n_boards=args.boards, n_steps=args.batch_steps)
+    probs = W.batch_boards(seed=4 + 100 * rank, n_boards=boards, n_steps=batch_steps)
     # tuned on the first 8 boards of the batch (same board distribution), cached per grid class
-    tuning = tune.tune(probs[:8], args.precision, steps=16, log=lambda m: print(m, file=sys.stderr))
+    tuning = tune.tune(probs[:8], precision, steps=16, log=lambda m: print(m, file=sys.stderr))
     cells = sum(p.cells * p.n_steps for p in probs)
 
-    def batched_solve():
+    def batched_solve(ps):
         b = solver.Batch(tuning=tuning)
-        sols = [solver.Solver(p, precision=args.precision) for p in probs]
+        sols = [solver.Solver(p, precision=precision) for p in ps]
         for s_ in sols:
             b.add(s_)
         done = 0
         while done < len(sols):
-            done = b.step(args.window)
+            done = b.step(window)
         b.sync()
         return b, sols
 
-    for _ in range(args.warmup):
-        b, sols = batched_solve()
+    for _ in range(warmup):   # same boards, a few chunks each: plans, graphs and pages warm
+        b, sols = batched_solve([p.replace(n_steps=min(p.n_steps, 2 * window)) for p in probs])
         b.close()
         for s_ in sols:
             s_.close()
@@ -348,10 +358,10 @@ def run_batched(args, world, rank, local):
         torch.distributed.barrier()
     times, last = [], None
     with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            b, sols = batched_solve()
+            b, sols = batched_solve(probs)
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
             if last is not None:
@@ -359,85 +369,109 @@ def run_batched(args, world, rank, local):
                     s_.close()
                 last[0].close()
             last = (b, sols)
-    el = sum(times)
-    el = _max_over_ranks(el)
-    value = len(probs) * args.steps * world / el
-    # per-board plain launches on the same GPU, and identity of the results
-    plain_t, plain_tr = _plain_solves(probs[: args.plain_boards], args.precision)
-    plain_rate = args.plain_boards / plain_t
-    diffs = [float(np.abs(last[1][q].traces() - plain_tr[q]).max()) for q in range(args.plain_boards)]
+    el = _max_over_ranks(sum(times))
+    value = len(probs) * steps * world / el
+    # per-board plain launches on the same GPU, same boards, and identity of the results
+    n_plain = min(plain_boards, len(probs))
+    with ClockSampler(local) as clk_plain:
+        plain_t, plain_tr = _plain_solves(probs[:n_plain], precision)
+    plain_t = _max_over_ranks(plain_t)
+    plain_rate = n_plain * world / plain_t
+    diffs = [float(np.abs(last[1][q].traces() - plain_tr[q]).max()) for q in range(n_plain)]
     for s_ in last[1]:
         s_.close()
     last[0].close()
-    return {"metric": METRIC, "value": round(value, 4), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
-            f"{args.precision}-storage/f32-compute", "data": "synthetic (seeded boards, sources, probes)",
-            "config": {"workload": f"batched: {len(probs)} boards (plane sides 20-120 mm, 1-3 pairs, dx=dy=0.5 mm, "
-                                   f"dz=0.2 mm, 6-cell air, 10-cell UPML), {args.batch_steps} steps each; "
-                                   "step = one batched solve of all boards",
-                       "cells_total": int(sum(p.cells for p in probs)), "tuning": tuning,
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
-            "gcell_updates_per_s": round(cells * args.steps * world / el / 1e9, 3),
-            "per_board_plain": {"solves_per_s": round(plain_rate, 4), "boards_timed": args.plain_boards,
-                                "speedup_batched": round(value / world / plain_rate, 3)},
-            "batched_vs_alone_max_abs_trace_diff": max(diffs),
-            "gpu_launches": None, "clocks": clk.summary(), "e2e": None}
+    return {"solves_per_s": round(value, 4), "unit": "solves/s", "boards": len(probs), "steps_per_board": batch_steps,
+            "cells_total": int(sum(p.cells for p in probs)), "timed_solves": steps, "wall_s": round(el, 3),
+            "gcell_updates_per_s": round(cells * steps * world / el / 1e9, 3), "tuning": tuning,
+            "plain": {"solves_per_s": round(plain_rate, 4), "boards": n_plain, "wall_s": round(plain_t, 3),
+                      "same_boards": n_plain == len(probs), "clocks": clk_plain.summary()},
+            "batched_over_plain": round(value / plain_rate, 3),
+            "batched_vs_alone_max_abs_trace_diff": max(diffs), "clocks": clk.summary()}
 
 
-def run_served(args, world, rank, local):
-    """Poisson request stream (mean 20 req/s) of multilayer boards, admitted by
-    HBM budget into one continuously batched mix; p50/p99 latency."""
+def served_record(requests, rate, step_scale, cell_scale, precision, window, hbm_budget_gb, world, rank, local,
+                  plain_requests):
+    """Poisson request stream of multilayer boards, admitted by HBM budget
+    into one continuously batched mix (p50/p99 latency, solves/s); the same
+    requests (the first `plain_requests`) served one at a time with
+    per-board launches, honouring the arrival times."""
+    import numpy as np
     import torch
-    from paper_1008_2602_gb300 import serve, workloads as W
+    from paper_1008_2602_gb300 import serve, solver, workloads as W
     torch.cuda.set_device(local)
-    reqs = W.request_stream(seed=5 + 100 * rank, n_requests=args.requests, rate=args.rate,
-                            step_scale=args.step_scale, cell_scale=args.cell_scale)
+    reqs = W.request_stream(seed=5 + 100 * rank, n_requests=requests, rate=rate,
+                            step_scale=step_scale, cell_scale=cell_scale)
     warm = W.request_stream(seed=99, n_requests=4, rate=1000.0, step_scale=0.02, cell_scale=0.05)
-    be = serve.CudaBackend(precision=args.precision)
-    serve.Server(be, hbm_budget=int(args.hbm_budget_gb * 2**30), chunk=args.window).run(warm)
+    be = serve.CudaBackend(precision=precision)
+    serve.Server(be, hbm_budget=int(hbm_budget_gb * 2**30), chunk=window).run(warm)
     be.close()
     if world > 1:
         torch.distributed.barrier()
-    be = serve.CudaBackend(precision=args.precision)
-    srv = serve.Server(be, hbm_budget=int(args.hbm_budget_gb * 2**30), chunk=args.window)
+    be = serve.CudaBackend(precision=precision)
+    srv = serve.Server(be, hbm_budget=int(hbm_budget_gb * 2**30), chunk=window)
     with ClockSampler(local) as clk:
         t0 = time.perf_counter()
         res = srv.run(reqs)
         wall = time.perf_counter() - t0
     be.close()
-    summ = serve.summarize(res, wall)
-    # the same stream served one request at a time (per-board plain launches)
-    from paper_1008_2602_gb300 import solver
-    t0 = time.perf_counter()
+    summ = serve.summarize(res, _max_over_ranks(wall))
+    summ["solves_per_s"] *= world
+    # the same requests one at a time (per-board plain launches)
+    n_plain = min(plain_requests, len(reqs))
     lat = []
-    start = time.perf_counter()
-    for r in reqs[: args.plain_requests]:
-        now = time.perf_counter() - start
-        if now < r.arrival:
-            time.sleep(r.arrival - now)
-        s_ = solver.Solver(r.problem, precision=args.precision)
-        s_.run()
-        s_.spectra()
-        s_.close()
-        lat.append(time.perf_counter() - start - r.arrival)
-    plain_wall = time.perf_counter() - t0
-    import numpy as np
-    return {"metric": METRIC, "value": round(summ["solves_per_s"], 4), "unit": "solves/s", "n_gpus": world,
-            "steps": 1, "warmup": 1, "ms_per_step": round(wall * 1e3, 1), "higher_is_better": True,
+    with ClockSampler(local) as clk_plain:
+        start = time.perf_counter()
+        for r in reqs[:n_plain]:
+            now = time.perf_counter() - start
+            if now < r.arrival:
+                time.sleep(r.arrival - now)
+            s_ = solver.Solver(r.problem, precision=precision)
+            s_.run()
+            s_.spectra()
+            s_.close()
+            lat.append(time.perf_counter() - start - r.arrival)
+        plain_wall = _max_over_ranks(time.perf_counter() - start)
+    plain_rate = n_plain * world / plain_wall
+    return {"solves_per_s": round(summ["solves_per_s"], 4), "unit": "solves/s",
+            "p50_latency_s": round(summ["p50_latency_s"], 4), "p99_latency_s": round(summ["p99_latency_s"], 4),
+            "requests": len(reqs), "rate_req_per_s": rate, "precision": precision, "chunk_steps": window,
+            "stream": f"lognormal cells median {2e6 * cell_scale:.3g} (max {40e6 * cell_scale:.3g}), "
+                      f"{int(2000 * step_scale)}-{int(20000 * step_scale)} steps, 4-32 probes",
+            "wall_s": round(summ["wall_s"], 3), "gcell_updates_per_s": round(summ["gcell_updates_per_s"], 3),
+            "plain": {"solves_per_s": round(plain_rate, 4), "requests": n_plain, "same_requests": n_plain == len(reqs),
+                      "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+                      "p99_latency_s": round(float(np.percentile(lat, 99)), 4), "clocks": clk_plain.summary()},
+            "served_over_plain": round(summ["solves_per_s"] / plain_rate, 3), "clocks": clk.summary()}
+
+
+def run_batched(args, world, rank, local):
+    rec = batched_record(args.boards, args.batch_steps, args.precision, args.window, args.steps, args.warmup, world,
+                         rank, local, args.plain_boards)
+    return {"metric": METRIC, "value": rec["solves_per_s"], "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(rec["wall_s"] / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else
+            f"{args.precision}-storage/f32-compute", "data": "synthetic (seeded boards, sources, probes)",
+            "config": {"workload": f"batched: {args.boards} boards (plane sides 20-120 mm, 1-3 pairs, dx=dy=0.5 mm, "
+                                   f"dz=0.2 mm, 6-cell air, 10-cell UPML), {args.batch_steps} steps each; "
+                                   "step = one batched solve of all boards",
+                       "cells_total": rec["cells_total"], "tuning": rec["tuning"],
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "batched": rec, "gpu_launches": None, "clocks": rec["clocks"], "e2e": None}
+
+
+def run_served(args, world, rank, local):
+    rec = served_record(args.requests, args.rate, args.step_scale, args.cell_scale, args.precision, args.window,
+                        args.hbm_budget_gb, world, rank, local, args.plain_requests)
+    return {"metric": METRIC, "value": rec["solves_per_s"], "unit": "solves/s", "n_gpus": world,
+            "steps": 1, "warmup": 1, "ms_per_step": round(rec["wall_s"] * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if args.precision == "fp32" else f"{args.precision}-storage/f32-compute",
             "data": "synthetic (seeded Poisson stream of boards)",
-            "config": {"workload": f"served: {args.requests} requests, Poisson {args.rate} req/s, lognormal cells "
-                                   f"(median {2e6 * args.cell_scale:.3g}, max {40e6 * args.cell_scale:.3g}), "
-                                   f"{int(2000 * args.step_scale)}-{int(20000 * args.step_scale)} steps, 4-32 probes",
+            "config": {"workload": f"served: {args.requests} requests, Poisson {args.rate} req/s, {rec['stream']}",
                        "chunk_steps": args.window, "hbm_budget_gb": args.hbm_budget_gb,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
-            "served": summ,
-            "per_request_plain": {"requests": len(lat), "solves_per_s": round(len(lat) / plain_wall, 4),
-                                  "p50_latency_s": float(np.percentile(lat, 50)),
-                                  "p99_latency_s": float(np.percentile(lat, 99))},
-            "gpu_launches": None, "clocks": clk.summary(), "e2e": None}
+            "served": rec, "gpu_launches": None, "clocks": rec["clocks"], "e2e": None}
 
 
 def run_reference(args, world, rank):
@@ -480,19 +514,24 @@ def main():
                     choices=["small", "realistic", "multilayer", "multilayer_h", "multilayer_q", "batched", "served"])
     ap.add_argument("--boards", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=5000)
-    ap.add_argument("--plain-boards", type=int, default=16)
+    ap.add_argument("--plain-boards", type=int, default=64, help="boards also solved one at a time (same set)")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--step-scale", type=float, default=1.0)
     ap.add_argument("--cell-scale", type=float, default=1.0)
-    ap.add_argument("--plain-requests", type=int, default=16)
+    ap.add_argument("--plain-requests", type=int, default=64, help="requests also served one at a time (same set)")
     ap.add_argument("--hbm-budget-gb", type=float, default=200.0)
     ap.add_argument("--window", type=int, default=200)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp16"])
     ap.add_argument("--tile-x", type=int, default=0, help="fused tile width (62 or 124 columns); 0 = tuned default")
     ap.add_argument("--tile-y", type=int, default=0, help="fused tile height (4 or 8 rows); 0 = tuned default")
     ap.add_argument("--zseg", type=int, default=0, help="fused z-segment length; 0 = tuned default")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched sub-record")
+    ap.add_argument("--no-served", action="store_true", help="default run: skip the served sub-records")
+    ap.add_argument("--sub-requests", type=int, default=24, help="default run: requests of the served sub-record")
+    ap.add_argument("--sub-step-scale", type=float, default=0.25)
+    ap.add_argument("--sub-cell-scale", type=float, default=0.25)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=6)
@@ -519,6 +558,20 @@ def main():
             torch.distributed.destroy_process_group()
         return
     out = run_single(args, world, rank, local)
+    # the batched and served halves of the metric, measured in the same run
+    # on their own workloads (compact records; --workload batched | served
+    # gives the full lines)
+    if not args.no_batched:
+        out["batched"] = batched_record(args.boards, args.batch_steps, args.precision, args.window, 1, 1, world, rank,
+                                        local, args.boards)
+    if not args.no_served:
+        out["served"] = served_record(args.sub_requests, args.rate, args.sub_step_scale, args.sub_cell_scale,
+                                      args.precision, args.window, args.hbm_budget_gb, world, rank, local,
+                                      args.sub_requests)
+        if args.precision == "fp32":
+            out["served_fp16"] = served_record(args.sub_requests, args.rate, args.sub_step_scale, args.sub_cell_scale,
+                                               "fp16", args.window, args.hbm_budget_gb, world, rank, local,
+                                               args.sub_requests)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args, args.cpu_sample_steps)

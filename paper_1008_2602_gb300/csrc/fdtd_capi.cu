@@ -936,16 +936,25 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         // box carries only the auxiliaries its own nodes need: faces graded
         // along one axis keep two, edges and corners six.  Per axis the node
         // ranges are low UPML, middle and high UPML; the z ranges of the
-        // outer boxes include the wall planes k = 0 and k = nz.
-        const int xs[4] = {0, h.ix0, h.ix1, nx + 1}, ys[4] = {0, h.iy0, h.iy1, ny + 1};
-        const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), nz + 1};
+        // outer boxes include the wall plane k = 0.
+        // A high wall plane (i = nx, j = ny or k = nz) behind a PEC wall holds
+        // no unknown: its tangential E edges are PEC, the normal H on it sees
+        // the curl of those zero edges, and the other samples do not exist.
+        // Everything there stays zero, so those planes are left out of the
+        // boxes (their zeros are still read as neighbours).  The low wall
+        // planes keep the H and E samples half a cell inside.
+        const int xe = bnd->wall[1] == FDTD_WALL_PEC ? nx : nx + 1;
+        const int ye = bnd->wall[3] == FDTD_WALL_PEC ? ny : ny + 1;
+        const int ze = bnd->wall[5] == FDTD_WALL_PEC ? nz : nz + 1;
+        const int xs[4] = {0, h.ix0, h.ix1, xe}, ys[4] = {0, h.iy0, h.iy1, ye};
+        const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), ze};
         for (int zb = 0; zb < 3; zb += 2) {
             // z-UPML layers with the wall plane: y strips over all x, then x strips
-            for (int yb = 0; yb < 3; yb += 2) boxes.push_back({0, nx + 1, ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
+            for (int yb = 0; yb < 3; yb += 2) boxes.push_back({0, xe, ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
             for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
             // the wall plane of the interior columns (the fused kernels start at k = 1)
             const int kw = zb == 0 ? 0 : nz;
-            boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
+            if (kw < ze) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
         }
         // planes between the z-UPML layers: y faces, x faces, the four corner columns
         for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});

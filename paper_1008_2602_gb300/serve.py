@@ -9,7 +9,10 @@ graph).  A board that reaches its step count retires at the next chunk
 boundary: its spectra are copied back, its device memory released and its
 latency (retire time - arrival time) recorded.  Requests that arrive while
 others are on the GPU join at the next chunk boundary, so their work overlaps
-on the device.
+on the device.  With a backend that can launch a chunk without waiting for
+it (``launch`` / ``wait``), admission runs while the chunk executes: a new
+board's host precompute and uploads (on its own stream) overlap the device
+work of the boards already admitted, and it joins the mix at the next chunk.
 
 The scheduling logic talks to a small backend interface so it can be
 exercised without a GPU; ``CudaBackend`` is the real one (libfdtd.so).
@@ -73,6 +76,14 @@ class CudaBackend:
         self.batch.step(n)
         self.batch.sync()
 
+    def launch(self, n: int) -> None:
+        """Queue one chunk of n steps for every member; returns at once."""
+        self.batch.step(n)
+
+    def wait(self) -> None:
+        """Wait for the queued chunk (and report device-side errors)."""
+        self.batch.sync()
+
     def remaining(self, handle) -> int:
         return self.batch.remaining(handle)
 
@@ -110,11 +121,18 @@ class Server:
         t0 = self.clock()
         sim_now = 0.0
         i = 0
-        while i < len(pending) or queue or self.active:
-            now = sim_now if self.simulate else self.clock() - t0
-            while i < len(pending) and pending[i].arrival * time_scale <= now:
+        overlap = not self.simulate and hasattr(self.backend, "launch") and hasattr(self.backend, "wait")
+
+        def now_():
+            return sim_now if self.simulate else self.clock() - t0
+
+        def arrivals():
+            nonlocal i
+            while i < len(pending) and pending[i].arrival * time_scale <= now_():
                 queue.append(pending[i])
                 i += 1
+
+        def admit():
             # admit in arrival order while a slot and the budget allow
             while queue and len(self.active) < self.max_boards:
                 req = queue[0]
@@ -129,9 +147,13 @@ class Server:
                 h = self.backend.admit(req.problem)
                 nb = max(need, self.backend.device_bytes(h))
                 self.used += nb
-                res = Result(rid=req.rid, arrival=req.arrival * time_scale, admitted=now, finished=math.nan,
+                res = Result(rid=req.rid, arrival=req.arrival * time_scale, admitted=now_(), finished=math.nan,
                              cells=req.problem.cells, steps=req.problem.n_steps)
                 self.active[req.rid] = (h, nb, res)
+
+        while i < len(pending) or queue or self.active:
+            arrivals()
+            admit()
             if not self.active:
                 if i < len(pending):          # idle until the next arrival
                     nxt = pending[i].arrival * time_scale
@@ -143,9 +165,14 @@ class Server:
             # one chunk for every admitted board
             if self.simulate:
                 sim_now += self.backend.step(self.chunk) or 0.0
+            elif overlap:
+                self.backend.launch(self.chunk)
+                arrivals()                    # boards admitted now join at the next chunk
+                admit()
+                self.backend.wait()
             else:
                 self.backend.step(self.chunk)
-            now = sim_now if self.simulate else self.clock() - t0
+            now = now_()
             for rid in [r for r, (h, _, _) in self.active.items() if self.backend.remaining(h) == 0]:
                 h, nb, res = self.active.pop(rid)
                 res.spectra = self.backend.retire(h)

@@ -2,6 +2,8 @@
 and a simulated clock (no GPU): admission by HBM budget and slot count,
 arrival order, chunked progress, latency accounting, rejection of requests
 that can never fit."""
+import time
+
 import numpy as np
 
 from paper_1008_2602_gb300 import serve, workloads as W
@@ -39,7 +41,7 @@ class FakeBackend:
         return h["left"]
 
     def retire(self, h):
-        self.active.remove(h)
+        self.active = [a for a in self.active if a is not h]   # by identity (boards hold numpy arrays)
         return np.zeros(1)
 
 
@@ -92,3 +94,43 @@ def test_summary_percentiles():
     s = serve.summarize(rs, wall=100.0)
     assert abs(s["p50_latency_s"] - 50.5) < 1e-9 and s["p99_latency_s"] > 99.0
     assert abs(s["solves_per_s"] - 1.0) < 1e-12
+
+
+class AsyncFakeBackend(FakeBackend):
+    """A backend whose chunk is queued by launch() and finished by wait(),
+    with real (short) durations, logging the order of calls."""
+
+    def __init__(self):
+        super().__init__()
+        self.log = []
+
+    def admit(self, prob):
+        self.log.append(("admit", prob.name))
+        return super().admit(prob)
+
+    def launch(self, n):
+        self.log.append(("launch", len(self.active)))
+        self._n = n
+        time.sleep(0.01)          # host time spent queueing the chunk
+
+    def wait(self):
+        time.sleep(0.01)          # device time of the chunk
+        self.step(self._n)
+        self.log.append(("wait", None))
+
+
+def test_admission_overlaps_the_running_chunk():
+    """Requests that arrive while a chunk is queued are admitted before the
+    server waits for that chunk (their host set-up overlaps device work),
+    join at the next chunk, and every request is served."""
+    reqs = _reqs(n=6, rate=1e6)
+    for k, r in enumerate(reqs):
+        r.arrival = 0.0 if k == 0 else 0.005   # one board first, the rest during its first chunk
+    be = AsyncFakeBackend()
+    srv = serve.Server(be, hbm_budget=1 << 40, chunk=10, simulate_clock=False)
+    res = srv.run(reqs)
+    assert sorted(r.rid for r in res) == [r.rid for r in reqs]
+    first_launch = be.log.index(("launch", 1))
+    first_wait = be.log.index(("wait", None))
+    admitted_between = [e for e in be.log[first_launch:first_wait] if e[0] == "admit"]
+    assert len(admitted_between) == 5, be.log[:12]

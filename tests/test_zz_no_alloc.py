@@ -75,11 +75,16 @@ def test_energy_static_matches_context_diagnostics_twice(upml, pad):
                                 ctypes.c_void_p(stream.cuda_stream), ctypes.byref(energy), ctypes.byref(divb))
         results.append((energy.value, divb.value, max(np.abs(f).max() for f in fields[6:])))
         del bufs
-    for (e_static, d_static, hmax), (_, e_ctx, d_ctx) in zip(results, states):
+    # div B outside the UPML is FP32 round-off accumulated over the run, so it
+    # is bounded by the largest |H| the run has seen (with UPML the fields
+    # later decay out of the board while that residue stays); a window one
+    # cell into the UPML gives a value above this bound
+    hmax_run = max(h for _, _, h in results)
+    bound = 1e-4 * MU0 * hmax_run / min(p.dx, p.dy, p.dz)
+    for (e_static, d_static, _), (_, e_ctx, d_ctx) in zip(results, states):
         assert e_ctx > 0
         assert abs(e_static - e_ctx) <= 1e-6 * e_ctx, (e_static, e_ctx)
-        bound = 1e-4 * MU0 * hmax / min(p.dx, p.dy, p.dz)   # same bound as the context's div B test
-        assert d_static <= bound and d_ctx <= bound
+        assert d_static <= bound and d_ctx <= bound, (d_static, d_ctx, bound)
         assert abs(d_static - d_ctx) <= bound
     assert results[0][0] != results[1][0]
     s.close()
