@@ -400,8 +400,11 @@ def served_record(requests, rate, step_scale, cell_scale, precision, window, hbm
     import torch
     from paper_1008_2602_gb300 import serve, solver, workloads as W
     torch.cuda.set_device(local)
-    reqs = W.request_stream(seed=5 + 100 * rank, n_requests=requests, rate=rate,
-                            step_scale=step_scale, cell_scale=cell_scale)
+    # one stream for the whole job; with several ranks the router gives each
+    # rank its share (no exchange between ranks)
+    reqs = W.request_stream(seed=5, n_requests=requests, rate=rate, step_scale=step_scale, cell_scale=cell_scale)
+    if world > 1:
+        reqs = [r for r, k in zip(reqs, serve.route(reqs, world)) if k == rank]
     warm = W.request_stream(seed=99, n_requests=4, rate=1000.0, step_scale=0.02, cell_scale=0.05)
     be = serve.CudaBackend(precision=precision)
     serve.Server(be, hbm_budget=int(hbm_budget_gb * 2**30), chunk=window).run(warm)
@@ -416,7 +419,7 @@ def served_record(requests, rate, step_scale, cell_scale, precision, window, hbm
         wall = time.perf_counter() - t0
     be.close()
     summ = serve.summarize(res, _max_over_ranks(wall))
-    summ["solves_per_s"] *= world
+    summ["solves_per_s"] = requests / summ["wall_s"]      # the whole stream over the slowest rank
     # the same requests one at a time (per-board plain launches)
     n_plain = min(plain_requests, len(reqs))
     lat = []
@@ -432,7 +435,7 @@ def served_record(requests, rate, step_scale, cell_scale, precision, window, hbm
             s_.close()
             lat.append(time.perf_counter() - start - r.arrival)
         plain_wall = _max_over_ranks(time.perf_counter() - start)
-    plain_rate = n_plain * world / plain_wall
+    plain_rate = (n_plain * world if world == 1 else requests * n_plain / max(len(reqs), 1)) / plain_wall
     return {"solves_per_s": round(summ["solves_per_s"], 4), "unit": "solves/s",
             "p50_latency_s": round(summ["p50_latency_s"], 4), "p99_latency_s": round(summ["p99_latency_s"], 4),
             "requests": len(reqs), "rate_req_per_s": rate, "precision": precision, "chunk_steps": window,

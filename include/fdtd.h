@@ -238,6 +238,34 @@ int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls);
  * FDTD_ENOMEM if the scratch cannot grow. */
 int fdtd_set_materials(fdtd_ctx *ctx, const uint8_t *mat_ids);
 
+/* Halo exchange for one board split into sub-boards along an axis (one
+ * sub-board per GPU, or several on one GPU).  On the Yee grid of Fig. 2 the
+ * curl of the Model section's leapfrog reaches one node plane, so sub-boards
+ * that share one cell layer stay exact if, after every step, each receives
+ * from its neighbour the E components tangential to the cut on the node
+ * plane it cannot compute itself (its outer wall plane there); H on the
+ * shared layer is recomputed on both sides from those E values.
+ * The plane is node plane `plane` (0 <= plane <= n along `axis`, 0 = x,
+ * 1 = y, 2 = z) of the components in comp_mask (bit f for FDTD_EX..FDTD_HZ),
+ * in the context's current state (E^n and H^{n-1/2} after n steps), in its
+ * storage type (FP32, or FP16 with the context's scale).
+ *  fdtd_halo_pack    copies the plane into dev_buf, a caller-owned device
+ *                    buffer of (number of components) x (the two other node
+ *                    counts) elements, component-major, rows along x (for a
+ *                    y plane: [comp][nz+1][nx+1]).
+ *  fdtd_halo_unpack  copies such a buffer back into the plane.
+ *  fdtd_halo_copy    copies the plane of src into plane dst_plane of dst
+ *                    (contexts on the same or on different devices, same
+ *                    storage type and scale, same extents on the other two
+ *                    axes, same step count), after the work queued on src's
+ *                    stream, on dst's stream.
+ * All three are asynchronous on the context's stream (dst's for the copy).
+ * Errors: FDTD_EINVAL (bad axis, plane, mask, shapes, NULL buffer),
+ * FDTD_ESTATE (a context in a batch; contexts at different steps). */
+int fdtd_halo_pack(fdtd_ctx *ctx, int axis, int plane, unsigned comp_mask, void *dev_buf);
+int fdtd_halo_unpack(fdtd_ctx *ctx, int axis, int plane, unsigned comp_mask, const void *dev_buf);
+int fdtd_halo_copy(fdtd_ctx *dst, int dst_plane, fdtd_ctx *src, int src_plane, int axis, unsigned comp_mask);
+
 /* Host only: the per-node edge coefficients fdtd_create builds for a
  * geometry (arguments as in fdtd_create), without touching a device.  The
  * coefficient of an E edge is 1/eps_r with eps_r the mean over the cells

@@ -92,6 +92,9 @@ _SIGS = {
     "fdtd_batch_sync": (c_int, [c_void_p]),
     "fdtd_batch_destroy": (None, [c_void_p]),
     "fdtd_set_tuning": (c_int, [c_void_p, P(fdtd_tuning)]),
+    "fdtd_halo_pack": (c_int, [c_void_p, c_int, c_int, ctypes.c_uint, c_void_p]),
+    "fdtd_halo_unpack": (c_int, [c_void_p, c_int, c_int, ctypes.c_uint, c_void_p]),
+    "fdtd_halo_copy": (c_int, [c_void_p, c_int, c_void_p, c_int, c_int, ctypes.c_uint]),
     "fdtd_batch_set_tuning": (c_int, [c_void_p, P(fdtd_tuning)]),
 }
 

@@ -78,6 +78,7 @@ struct fdtd_ctx {
     std::vector<fdtd_box> boxes;
     std::vector<uint8_t> mask;
     int prec = FDTD_FP32;
+    int device = 0;             // CUDA device the context's memory lives on
     double dt = 0.0;
     // host mirror of the device descriptor
     Board h{};
@@ -860,6 +861,7 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
                          : grid->courant / (kC0 * std::sqrt(1.0 / (grid->dx * grid->dx) + 1.0 / (grid->dy * grid->dy) +
                                                              1.0 / (grid->dz * grid->dz)));
     c->grid_cap = device_grid_cap();
+    if (cudaGetDevice(&c->device) != cudaSuccess) { cudaGetLastError(); c->device = 0; }
     static bool smem_limits = false;
     if (!smem_limits) {
         cudaError_t e = fused_set_smem_limits();
@@ -949,8 +951,12 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         const int xs[4] = {0, h.ix0, h.ix1, xe}, ys[4] = {0, h.iy0, h.iy1, ye};
         const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), ze};
         for (int zb = 0; zb < 3; zb += 2) {
-            // z-UPML layers with the wall plane: y strips over all x, then x strips
-            for (int yb = 0; yb < 3; yb += 2) boxes.push_back({0, xe, ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
+            // z-UPML layers with the wall plane: y strips cut where the x
+            // grading starts (each piece then keeps only the auxiliaries of
+            // its own graded axes: on a sub-board whose y face is a cut, not
+            // a UPML, the middle is a plain z face), then x strips
+            for (int yb = 0; yb < 3; yb += 2)
+                for (int xb = 0; xb < 3; ++xb) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
             for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
             // the wall plane of the interior columns (the fused kernels start at k = 1)
             const int kw = zb == 0 ? 0 : nz;
@@ -1468,6 +1474,112 @@ int fdtd_selftest_wait_timeout(void *stream, unsigned max_polls)
     cudaFree(d);
     if (e != cudaSuccess) return cuda_fail(e, "selftest");
     if (status & 2) return fail(FDTD_ETIMEOUT, "bounded device wait gave up (self-test: expected)");
+    return FDTD_OK;
+}
+
+namespace {
+
+// Node plane `p` along `axis` of one field array as a 2D copy: `height` rows
+// of `width` elements, `spitch` elements apart, starting `off` elements in.
+// (x planes: one element per (j, k) row, the rows a pitch apart; y planes:
+// one x row per k, a plane apart; z planes: the ny+1 x rows of plane p.)
+struct PlaneGeom {
+    size_t off, width, height, spitch;
+};
+
+bool plane_geom(const Board &h, int axis, int p, PlaneGeom &g)
+{
+    const int n[3] = {h.nx, h.ny, h.nz};
+    if (axis < 0 || axis > 2 || p < 0 || p > n[axis]) return false;
+    if (axis == 0) g = {(size_t)p, 1, (size_t)(h.ny + 1) * (h.nz + 1), (size_t)h.pitch};
+    else if (axis == 1) g = {(size_t)p * h.pitch, (size_t)h.nx + 1, (size_t)h.nz + 1, (size_t)h.plane};
+    else g = {(size_t)p * h.plane, (size_t)h.nx + 1, (size_t)h.ny + 1, (size_t)h.pitch};
+    return true;
+}
+
+int check_halo(const fdtd_ctx *c, int axis, int plane, unsigned mask, PlaneGeom &g)
+{
+    if (!c) return fail(FDTD_EINVAL, "NULL context");
+    if (c->batch) return fail(FDTD_ESTATE, "context is in a batch");
+    if (mask == 0 || (mask & ~0x3Fu)) return fail(FDTD_EINVAL, "component mask must be a non-empty subset of 0x3F");
+    if (!plane_geom(c->h, axis, plane, g)) return fail(FDTD_EINVAL, "axis must be 0..2 and plane 0..n along it");
+    return FDTD_OK;
+}
+
+}  // namespace
+
+int fdtd_halo_pack(fdtd_ctx *c, int axis, int plane, unsigned comp_mask, void *dev_buf)
+{
+    PlaneGeom g{};
+    if (int r = check_halo(c, axis, plane, comp_mask, g)) return r;
+    if (!dev_buf) return fail(FDTD_EINVAL, "NULL buffer");
+    if (int r = finalize(c)) return r;
+    const size_t es = elem_size(c->prec);
+    const int par = (int)(c->host_step & 1);
+    unsigned char *o = static_cast<unsigned char *>(dev_buf);
+    for (int f = 0; f < 6; ++f) {
+        if (!(comp_mask & (1u << f))) continue;
+        const unsigned char *src = static_cast<const unsigned char *>(c->h.f[par][f]) + g.off * es;
+        CK(cudaMemcpy2DAsync(o, g.width * es, src, g.spitch * es, g.width * es, g.height, cudaMemcpyDeviceToDevice,
+                             c->cur));
+        o += g.width * g.height * es;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_halo_unpack(fdtd_ctx *c, int axis, int plane, unsigned comp_mask, const void *dev_buf)
+{
+    PlaneGeom g{};
+    if (int r = check_halo(c, axis, plane, comp_mask, g)) return r;
+    if (!dev_buf) return fail(FDTD_EINVAL, "NULL buffer");
+    if (int r = finalize(c)) return r;
+    const size_t es = elem_size(c->prec);
+    const int par = (int)(c->host_step & 1);
+    const unsigned char *in = static_cast<const unsigned char *>(dev_buf);
+    for (int f = 0; f < 6; ++f) {
+        if (!(comp_mask & (1u << f))) continue;
+        unsigned char *dst = static_cast<unsigned char *>(c->h.f[par][f]) + g.off * es;
+        CK(cudaMemcpy2DAsync(dst, g.spitch * es, in, g.width * es, g.width * es, g.height, cudaMemcpyDeviceToDevice,
+                             c->cur));
+        in += g.width * g.height * es;
+    }
+    return FDTD_OK;
+}
+
+int fdtd_halo_copy(fdtd_ctx *dst, int dst_plane, fdtd_ctx *src, int src_plane, int axis, unsigned comp_mask)
+{
+    PlaneGeom gd{}, gs{};
+    if (int r = check_halo(dst, axis, dst_plane, comp_mask, gd)) return r;
+    if (int r = check_halo(src, axis, src_plane, comp_mask, gs)) return r;
+    if (dst == src) return fail(FDTD_EINVAL, "source and destination must be different contexts");
+    if (dst->prec != src->prec) return fail(FDTD_EINVAL, "the two contexts store fields in different precisions");
+    if (gd.width != gs.width || gd.height != gs.height)
+        return fail(FDTD_EINVAL, "the planes differ in shape (the sub-boards must agree on the two other axes)");
+    if (dst->host_step != src->host_step) return fail(FDTD_ESTATE, "the two contexts are at different steps");
+    if (int r = finalize(dst)) return r;
+    if (int r = finalize(src)) return r;
+    if (src->h.scale != dst->h.scale) return fail(FDTD_EINVAL, "the two contexts use different storage scales");
+    // the copy runs on the destination's stream once the source's queued work is done
+    cudaEvent_t ev = nullptr;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    cudaError_t e = cudaEventRecord(ev, src->cur);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->cur, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "halo copy ordering");
+    const size_t es = elem_size(dst->prec);
+    const int par = (int)(dst->host_step & 1);
+    for (int f = 0; f < 6; ++f) {
+        if (!(comp_mask & (1u << f))) continue;
+        cudaMemcpy3DPeerParms p{};
+        p.srcPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(src->h.f[par][f]) + gs.off * es, gs.spitch * es,
+                                       gs.width * es, gs.height);
+        p.srcDevice = src->device;
+        p.dstPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(dst->h.f[par][f]) + gd.off * es, gd.spitch * es,
+                                       gd.width * es, gd.height);
+        p.dstDevice = dst->device;
+        p.extent = make_cudaExtent(gs.width * es, gs.height, 1);
+        CK(cudaMemcpy3DPeerAsync(&p, dst->cur));
+    }
     return FDTD_OK;
 }
 

@@ -47,7 +47,7 @@
 
 namespace fdtd {
 
-constexpr int kMaxSlab = 18;
+constexpr int kMaxSlab = 26;
 constexpr int kPitchAlign = 64;
 constexpr int kMaxCombo = 256;
 constexpr int kMaxCombo16 = 65536;

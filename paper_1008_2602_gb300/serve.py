@@ -182,6 +182,27 @@ class Server:
         return self.results
 
 
+def route(requests, n_ranks: int, rate_cells_per_s: float = 6e10) -> List[int]:
+    """Rank for every request of one stream shared by n_ranks replicas (one
+    GPU each): in arrival order, each request goes to the rank with the least
+    estimated backlog (cell-updates still queued, drained at
+    rate_cells_per_s per rank since the previous arrival).  Deterministic in
+    its inputs, so every rank computes the same assignment and serves its own
+    share with no exchange between ranks."""
+    backlog = [0.0] * n_ranks
+    t_prev = 0.0
+    out = []
+    for r in sorted(requests, key=lambda q: (q.arrival, q.rid)):
+        drain = rate_cells_per_s * max(0.0, r.arrival - t_prev)
+        t_prev = max(t_prev, r.arrival)
+        backlog = [max(0.0, b - drain) for b in backlog]
+        k = min(range(n_ranks), key=lambda i: (backlog[i], i))
+        backlog[k] += float(r.problem.cells) * r.problem.n_steps
+        out.append((r.rid, k))
+    order = {rid: k for rid, k in out}
+    return [order[r.rid] for r in requests]
+
+
 def summarize(results: List[Result], wall: float) -> dict:
     lat = np.array([r.latency for r in results]) if results else np.zeros(1)
     cells_steps = float(sum(r.cells * r.steps for r in results))

@@ -1,8 +1,10 @@
 """Multi-GPU host logic on CPU: ``bench.py --gpus N`` runs N independent
-replicas (one board, batch or request stream per rank, no data-path
-collective) and reports the whole-job throughput over the slowest rank.
-Here two gloo ranks on 127.0.0.1 check the cross-rank max and that the
-replicas draw different seeded inputs of the same shape."""
+replicas (one board or batch per rank, no data-path collective; the served
+stream is one stream split across the ranks by ``serve.route``) and reports
+the whole-job throughput over the slowest rank.  Here two gloo ranks on
+127.0.0.1 check the cross-rank max, that the replicas draw different seeded
+inputs of the same shape, and that the routed stream is served exactly once
+across the ranks."""
 import os
 import socket
 import sys
@@ -76,3 +78,42 @@ def test_max_over_ranks_is_identity_without_a_process_group():
     import bench
     assert not dist.is_initialized()
     assert bench._max_over_ranks(3.25) == 3.25
+
+
+def _route_rank(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    try:
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+        from paper_1008_2602_gb300 import serve, workloads as W
+        from test_serve import FakeBackend
+        reqs = W.request_stream(seed=5, n_requests=30, rate=40.0, step_scale=0.05, cell_scale=0.02)
+        mine = [r for r, k in zip(reqs, serve.route(reqs, world)) if k == rank]
+        res = serve.Server(FakeBackend(), hbm_budget=1 << 40, chunk=50, simulate_clock=True).run(mine)
+        out = [None] * world
+        dist.all_gather_object(out, sorted(x.rid for x in res))
+        dist.barrier()
+        dist.destroy_process_group()
+        q.put((rank, out, [r.rid for r in reqs]))
+    except Exception as e:
+        q.put((rank, None, repr(e)))
+
+
+def test_routed_stream_is_served_once_across_two_gloo_ranks():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_route_rank, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = dict((rank, (out, all_ids)) for rank, out, all_ids in (q.get(timeout=240) for _ in range(world)))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out, all_ids = res[0]
+    assert out is not None, all_ids
+    assert res[1][0] == out                              # every rank gathered the same shares
+    assert sorted(out[0] + out[1]) == sorted(all_ids)   # each request served exactly once
+    assert out[0] and out[1]                             # both ranks got work

@@ -134,3 +134,18 @@ def test_admission_overlaps_the_running_chunk():
     first_wait = be.log.index(("wait", None))
     admitted_between = [e for e in be.log[first_launch:first_wait] if e[0] == "admit"]
     assert len(admitted_between) == 5, be.log[:12]
+
+
+def test_router_balances_one_stream_across_ranks():
+    """route(): every request to exactly one rank, deterministic, and the
+    cell-updates per rank balanced (largest share within 1.5x of the mean on
+    a burst where all requests arrive at once)."""
+    reqs = W.request_stream(seed=8, n_requests=40, rate=1e6, step_scale=0.05, cell_scale=0.02)
+    ranks = serve.route(reqs, 4)
+    assert ranks == serve.route(reqs, 4)
+    assert set(ranks) <= {0, 1, 2, 3} and len(ranks) == len(reqs)
+    work = [0.0] * 4
+    for r, k in zip(reqs, ranks):
+        work[k] += r.problem.cells * r.problem.n_steps
+    assert max(work) <= 1.5 * (sum(work) / 4)
+    assert serve.route(reqs, 1) == [0] * len(reqs)
