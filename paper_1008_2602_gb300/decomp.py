@@ -248,7 +248,9 @@ class DistributedSplitSolver:
         self.rank = rank
         self.split = split_y(prob, even_cuts(prob, world))
         self.part = self.split.parts[rank]
-        self.stream = torch.cuda.current_stream()
+        # one stream for the library's work and the torch copies and
+        # transfers of the exchange, so that they are ordered
+        self.stream = torch.cuda.Stream()
         self.s = solver.Solver(self.part.problem, precision=precision, stream=self.stream, tuning=tuning)
         self.es = 4 if precision == "fp32" else 2
         self.dtype = torch.float32 if precision == "fp32" else torch.float16
@@ -265,7 +267,7 @@ class DistributedSplitSolver:
         def pack(plane):
             buf = torch.empty(self.count, dtype=self.dtype, device=dev)
             C.fdtd_halo_pack(self.s.ctx, 1, plane, TANGENTIAL_Y, buf.data_ptr())
-            return buf if nccl else (self.stream.synchronize(), buf.cpu())[1]
+            return buf if nccl else buf.cpu()
 
         def unpack(plane, h):
             buf = h[1] if nccl else h[1].to(dev)
@@ -282,7 +284,8 @@ class DistributedSplitSolver:
             for w, _ in handles:
                 w.wait()
 
-        exchange_ranks(self.split, self.rank, pack, unpack, send, recv, wait)
+        with torch.cuda.stream(self.stream):
+            exchange_ranks(self.split, self.rank, pack, unpack, send, recv, wait)
 
     def step(self, n: int) -> "DistributedSplitSolver":
         for _ in range(int(n)):
