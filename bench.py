@@ -199,7 +199,7 @@ def run_single(args, world, rank, local):
 
     if world > 1:
         torch.distributed.barrier()
-    phase = np.zeros(7)
+    phase = np.zeros(6)
     with ClockSampler(dev) as clk:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -220,21 +220,16 @@ def run_single(args, world, rank, local):
     es = 4 if args.precision == "fp32" else 2
     bytes_per_node = 12 * es + (2 if inf["n_combo"] > 256 else 1)
     upml_nodes = inf["fused_upml_nodes"]
-    yg_nodes = inf["fused_ygraded_nodes"]
-    int_nodes = interior_nodes - upml_nodes - yg_nodes
+    int_nodes = interior_nodes - upml_nodes
     alg_bytes = bytes_per_node * int_nodes
     n_launch = window * args.steps
-    t_int = phase[3] / 1e3 / n_launch
+    t_int = phase[2] / 1e3 / n_launch
     t_zp = phase[1] / 1e3 / n_launch
-    t_yg = phase[2] / 1e3 / n_launch
     achieved = alg_bytes / t_int / 1e9
     zp_bytes = (bytes_per_node + 16) * upml_nodes
-    yg_bytes = (bytes_per_node + 16) * yg_nodes     # + D~y read/written, B~y read and written to the other parity
-    # whole leapfrog step: every node's 12 field values + id, the fused
-    # launches' z- and y-UPML auxiliaries and the slab auxiliaries (each read
-    # and written once)
-    step_bytes = (bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 16 * (upml_nodes + yg_nodes)
-                  + 8 * inf["slab_aux_values"])
+    # whole leapfrog step: every node's 12 field values + id, the z-UPML
+    # auxiliaries and the slab auxiliaries (each read and written once)
+    step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 16 * upml_nodes + 8 * inf["slab_aux_values"]
     t_leap = elapsed / (window * args.steps)
     peak, peak_kind = _measured_peaks()
     traffic = _traffic_for(f"k_fused_interior_{args.precision}", int_nodes)
@@ -273,8 +268,7 @@ def run_single(args, world, rank, local):
         "config": {**_describe(prob, args.workload, window, args.precision),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "phase_ms_per_leapfrog_step": {k: round(v / n_launch, 5) for k, v in
-                                       zip(["slab_h", "fused_zupml", "fused_yface", "fused_interior", "slab_e", "post",
-                                            "dft_total"],
+                                       zip(["slab_h", "fused_zupml", "fused_interior", "slab_e", "post", "dft_total"],
                                            phase)},
         "roofline": {"bound": "hbm", "kernel": "k_fused interior launch (fused H+E, planes outside the z-UPML)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
@@ -291,14 +285,9 @@ def run_single(args, world, rank, local):
                            "units_per_launch": upml_nodes, "mean_launch_ms": round(t_zp * 1e3, 5),
                            "achieved": round(zp_bytes / t_zp / 1e9, 1) if t_zp > 0 else None,
                            "frac": round(zp_bytes / t_zp / 1e9 / peak, 4) if t_zp > 0 else None},
-        "roofline_yface": {"kernel": "k_fused y-face launch (y-UPML rows of the interior planes)",
-                           "bytes_per_unit": bytes_per_node + 16, "units_per_launch": yg_nodes,
-                           "mean_launch_ms": round(t_yg * 1e3, 5),
-                           "achieved": round(yg_bytes / t_yg / 1e9, 1) if t_yg > 0 else None,
-                           "frac": round(yg_bytes / t_yg / 1e9 / peak, 4) if t_yg > 0 else None},
         "tuning": {"tile_x": args.tile_x or "default", "tile_y": args.tile_y or "default",
                    "zseg": args.zseg or "default"},
-        "gpu_launches": int(args.steps * (window * (4 + (1 if upml_nodes else 0) + (1 if yg_nodes else 0)) + 2)),
+        "gpu_launches": int(args.steps * (window * (5 if upml_nodes else 4) + 2)),
         "clocks": clk.summary(),
         "e2e": e2e,
         "device_ms_in_timed_region": round(dev_ms, 3),

@@ -93,13 +93,12 @@ typedef struct {
     int n_total_steps;         /* DFT length N set by fdtd_set_spectrum (0 if unset) */
     int n_bins;                /* DFT bins q = 0..n_bins-1, f_q = q / (N dt) */
     int precision;
-    long long interior_nodes;  /* nodes updated by the fused H+E kernel (all three launches) */
+    long long interior_nodes;  /* nodes updated by the fused interior kernel */
     long long fused_upml_nodes;/* of those, nodes in z-UPML planes (carry D~z and B~z) */
     long long slab_nodes;      /* nodes updated by the UPML/boundary slab kernels */
     long long device_bytes;    /* device memory held */
     int n_combo;               /* distinct per-node E-coefficient triples */
     long long slab_aux_values; /* auxiliary D~/B~ values held by the slabs (read and written once per step) */
-    long long fused_ygraded_nodes; /* of those, nodes of the y-face launch (y-UPML rows, carry D~y and B~y) */
 } fdtd_info_t;
 
 /* Create a board (Model section, Fig. 1).
@@ -166,13 +165,12 @@ int fdtd_set_spectrum(fdtd_ctx *ctx, double f_max, int n_total_steps);
 int fdtd_step(fdtd_ctx *ctx, int n);
 
 /* fdtd_step with every phase launched directly (no CUDA graph) and timed
- * with CUDA events on the context's stream: phase_ms[0..6] receive the summed
+ * with CUDA events on the context's stream: phase_ms[0..5] receive the summed
  * device time [ms] of the UPML/boundary slab H kernel, the fused H+E kernel
  * over the z-UPML planes of the interior columns, the fused H+E kernel over
- * the y-UPML rows of the interior planes, the fused H+E kernel over the
- * interior planes' remaining rows, the slab E kernel, the source/probe kernel
- * and the running-DFT update over the n steps.  Synchronises.  phase_ms (7
- * doubles) may not be NULL. */
+ * the interior planes, the slab E kernel, the source/probe kernel and the
+ * running-DFT update over the n steps.  Synchronises.  phase_ms (6 doubles)
+ * may not be NULL. */
 int fdtd_step_profiled(fdtd_ctx *ctx, int n, double *phase_ms);
 
 /* Copy the running DFT to host out[P][Q][2] (re, im), P = probes, Q = bins;

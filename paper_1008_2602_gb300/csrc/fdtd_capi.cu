@@ -108,7 +108,6 @@ struct fdtd_ctx {
     int grid_cap = 0;
     std::vector<cudaEvent_t> events; // fdtd_step_profiled
     size_t zaux_n[2] = {0, 0};       // elements per fused-region z-UPML auxiliary array
-    size_t yaux_n[2] = {0, 0};       // elements per y-UPML-row auxiliary array of the interior launch
     long long zplanes[2] = {0, 0};   // planes of the two z-UPML boxes
     CUtensorMap *tm_dev = nullptr;   // kNumMaps descriptors in device memory
 };
@@ -590,21 +589,15 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
 }
 
 // Fused-kernel items of a board: (x tile, y tile, z segment), x fastest.  The
-// interior launch covers planes [iz0, iz1) and rows [iy0, iy1), the z-UPML
-// launch planes [1, iz0) and [max(iz1, iz0), nz), the y-face launch the
-// y-UPML rows [fy0, iy0) and [iy1, fy1) of the interior planes (each face
-// tiled on its own); the device decodes items the same way.
-enum FusedKind { kInterior = 0, kZUpml = 1, kYFace = 2 };
-long long fused_items(const Board &h, const fdtd_tuning &t, int kind)
+// interior launch covers planes [iz0, iz1), the z-UPML launch [1, iz0) and
+// [max(iz1, iz0), nz); the device decodes items the same way.
+long long fused_items(const Board &h, const fdtd_tuning &t, bool zp)
 {
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0;
     if (Lx <= 0 || Ly <= 0 || h.nz < 2) return 0;
     auto segs = [&](long long k0, long long k1) { return k1 > k0 ? (k1 - k0 + t.zseg - 1) / t.zseg : 0; };
-    auto rows = [&](long long n) { return n > 0 ? (n + t.tile_y - 1) / t.tile_y : 0; };
-    const long long ntx = (Lx + t.tile_x - 1) / t.tile_x;
-    if (kind == kZUpml) return ntx * rows(Ly) * (segs(1, h.iz0) + segs(std::max(h.iz1, h.iz0), h.nz));
-    if (kind == kYFace) return ntx * (rows(h.iy0 - h.fy0) + rows(h.fy1 - h.iy1)) * segs(h.iz0, h.iz1);
-    return ntx * rows(Ly) * segs(h.iz0, h.iz1);
+    const long long nseg = zp ? segs(1, h.iz0) + segs(std::max(h.iz1, h.iz0), h.nz) : segs(h.iz0, h.iz1);
+    return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * nseg;
 }
 
 long long dft_items(const Board &h)
@@ -613,8 +606,7 @@ long long dft_items(const Board &h)
     return (long long)h.n_bins * ((h.n_probe + kDftProbeGroup - 1) / kDftProbeGroup);
 }
 
-// Lay out plan arrays [boards | int_prefix | zp_prefix | slab_prefix | dft_prefix | yg_prefix | work | slab
-// blocks] in buf.
+// Lay out plan arrays [boards | int_prefix | zp_prefix | slab_prefix | dft_prefix | work | slab blocks] in buf.
 int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long long *&buf, size_t &cap,
                Plan &plan, cudaStream_t st, std::vector<long long> &host)
 {
@@ -628,18 +620,17 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     long long n_slab_blk = 0;
     for (int b = 0; b < nb; ++b) n_slab_blk += boards[b]->h.slab_blocks;
     static_assert(sizeof(SlabBlock) == 4 * sizeof(long long), "slab block descriptor layout");
-    const size_t head = ((size_t)nb + 5 * ((size_t)nb + 1) + 2 + 1) & ~(size_t)1;   // + three work counters, 16-byte aligned
+    const size_t head = ((size_t)nb + 4 * ((size_t)nb + 1) + 1 + 1) & ~(size_t)1;   // + two work counters, 16-byte aligned
     const size_t words = head + 4 * (size_t)n_slab_blk;
     host.assign(words, 0);
     long long *ptrs = host.data();
-    long long *ip = ptrs + nb, *zp = ip + nb + 1, *sp = zp + nb + 1, *dp = sp + nb + 1, *yp = dp + nb + 1;
+    long long *ip = ptrs + nb, *zp = ip + nb + 1, *sp = zp + nb + 1, *dp = sp + nb + 1;
     SlabBlock *sb = reinterpret_cast<SlabBlock *>(ptrs + head);
     for (int b = 0; b < nb; ++b) {
         const Board &h = boards[b]->h;
         ptrs[b] = (long long)(uintptr_t)boards[b]->d;
-        ip[b + 1] = ip[b] + fused_items(h, t, kInterior);
-        zp[b + 1] = zp[b] + fused_items(h, t, kZUpml);
-        yp[b + 1] = yp[b] + fused_items(h, t, kYFace);
+        ip[b + 1] = ip[b] + fused_items(h, t, false);
+        zp[b + 1] = zp[b] + fused_items(h, t, true);
         sp[b + 1] = sp[b] + h.slab_blocks;
         dp[b + 1] = dp[b] + dft_items(h);
         for (int s = 0; s < h.n_slab; ++s) {
@@ -675,13 +666,11 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.zp_prefix = buf + nb + (nb + 1);
     plan.slab_prefix = buf + nb + 2 * (nb + 1);
     plan.dft_prefix = buf + nb + 3 * (nb + 1);
-    plan.yg_prefix = buf + nb + 4 * (nb + 1);
     plan.n_int = ip[nb];
     plan.n_zp = zp[nb];
-    plan.n_yg = yp[nb];
     plan.n_slab = sp[nb];
     plan.n_dft = dp[nb];
-    plan.work = (int *)(buf + nb + 5 * (nb + 1));
+    plan.work = (int *)(buf + nb + 4 * (nb + 1));
     plan.slab_blk = reinterpret_cast<const SlabBlock *>(buf + head);
     return FDTD_OK;
 }
@@ -940,18 +929,8 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     h.iz0 = std::max(bnd->depth[4], 1); h.iz1 = nz - bnd->depth[5];
     std::vector<std::array<int, 6>> boxes;
     const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
-    // The y-face launch of the fused kernel works the y-UPML rows of the
-    // interior planes: a graded y face is PEC-backed, so its wall plane j = 0
-    // holds only the samples half a cell inside (and the tangential E there
-    // is PEC), and j = ny none.
-    h.fy0 = h.iy0;
-    h.fy1 = h.iy1;
-    if (fused && h.iz1 > h.iz0) {
-        if (bnd->depth[2] > 0) h.fy0 = 0;
-        if (bnd->depth[3] > 0) h.fy1 = ny;
-    }
     if (!fused) {
-        h.ix0 = h.ix1 = h.iy0 = h.iy1 = h.fy0 = h.fy1 = 0;
+        h.ix0 = h.ix1 = h.iy0 = h.iy1 = 0;
         h.iz0 = 1; h.iz1 = nz;
         boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
     } else {
@@ -983,10 +962,8 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
             const int kw = zb == 0 ? 0 : nz;
             if (kw < ze) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
         }
-        // planes between the z-UPML layers: y faces (unless the y-face launch
-        // works them), x faces, the four corner columns
-        if (h.fy0 == h.iy0) boxes.push_back({h.ix0, h.ix1, ys[0], ys[1], zs[1], zs[2]});
-        if (h.fy1 == h.iy1) boxes.push_back({h.ix0, h.ix1, ys[2], ys[3], zs[1], zs[2]});
+        // planes between the z-UPML layers: y faces, x faces, the four corner columns
+        for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});
         for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[1], zs[2]});
         for (int yb = 0; yb < 3; yb += 2)
             for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[1], zs[2]});
@@ -1053,27 +1030,6 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         h.zB[bx][0] = ptr[1];
         h.zB[bx][1] = ptr[2];
         c->zaux_n[bx] = n;
-    }
-    // B~y (two parities) and D~y of the interior launch's y-UPML rows
-    h.ycol0 = h.ix0 & ~1;
-    h.ypitch = ((h.ix1 + 1 - h.ycol0) + 63) & ~63;
-    h.yj0[0] = h.fy0; h.yrows[0] = h.iy0 - h.fy0;
-    h.yj0[1] = h.iy1; h.yrows[1] = h.fy1 - h.iy1;
-    for (int bx = 0; bx < 2; ++bx) {
-        h.yD[bx] = nullptr;
-        h.yB[bx][0] = h.yB[bx][1] = nullptr;
-        c->yaux_n[bx] = 0;
-        if (!fused || h.yrows[bx] <= 0 || h.iz1 <= h.iz0) continue;
-        const size_t n = (size_t)(h.iz1 - h.iz0) * h.yrows[bx] * h.ypitch;
-        float *ptr[3] = {nullptr, nullptr, nullptr};   // D~y, B~y (two parities)
-        for (int t = 0; t < 3 && !r; ++t) {
-            r = dalloc(c, &ptr[t], sizeof(float) * n);
-            if (!r) { cudaError_t e = cudaMemsetAsync(ptr[t], 0, sizeof(float) * n, c->cur); if (e) r = cuda_fail(e, "memset"); }
-        }
-        h.yD[bx] = ptr[0];
-        h.yB[bx][0] = ptr[1];
-        h.yB[bx][1] = ptr[2];
-        c->yaux_n[bx] = n;
     }
     h.slab_blocks = blocks;
     long long *ctr = nullptr;
@@ -1383,9 +1339,6 @@ int fdtd_reset(fdtd_ctx *c)
         if (h.zD[bx]) CK(cudaMemsetAsync(h.zD[bx], 0, sizeof(float) * c->zaux_n[bx], c->cur));
         for (int p = 0; p < 2; ++p)
             if (h.zB[bx][p]) CK(cudaMemsetAsync(h.zB[bx][p], 0, sizeof(float) * c->zaux_n[bx], c->cur));
-        if (h.yD[bx]) CK(cudaMemsetAsync(h.yD[bx], 0, sizeof(float) * c->yaux_n[bx], c->cur));
-        for (int p = 0; p < 2; ++p)
-            if (h.yB[bx][p]) CK(cudaMemsetAsync(h.yB[bx][p], 0, sizeof(float) * c->yaux_n[bx], c->cur));
     }
     if (h.trace) CK(cudaMemsetAsync(h.trace, 0, sizeof(float) * (size_t)h.n_probe * h.n_total, c->cur));
     if (h.dft) CK(cudaMemsetAsync(h.dft, 0, sizeof(double) * 2 * (size_t)h.n_probe * std::max(h.n_bins, 1), c->cur));
@@ -1424,9 +1377,6 @@ void ckpt_regions(const fdtd_ctx *c, std::vector<std::pair<void *, size_t>> &out
         if (h.zD[bx]) out.push_back({h.zD[bx], sizeof(float) * c->zaux_n[bx]});
         for (int p = 0; p < 2; ++p)
             if (h.zB[bx][p]) out.push_back({h.zB[bx][p], sizeof(float) * c->zaux_n[bx]});
-        if (h.yD[bx]) out.push_back({h.yD[bx], sizeof(float) * c->yaux_n[bx]});
-        for (int p = 0; p < 2; ++p)
-            if (h.yB[bx][p]) out.push_back({h.yB[bx][p], sizeof(float) * c->yaux_n[bx]});
     }
     if (h.trace) out.push_back({h.trace, sizeof(float) * (size_t)h.n_probe * h.n_total});
     if (h.dft) out.push_back({h.dft, sizeof(double) * 2 * (size_t)h.n_probe * std::max(h.n_bins, 1)});
@@ -1717,11 +1667,8 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     info->n_bins = h.n_bins;
     info->precision = c->prec;
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
-    const bool fr = Lx > 0 && Ly > 0 && Lz > 0;
-    const long long zpl = c->zplanes[0] + c->zplanes[1], ipl = fr ? Lz - zpl : 0;
-    info->fused_upml_nodes = fr ? Lx * Ly * zpl : 0;
-    info->fused_ygraded_nodes = fr ? Lx * ((long long)(h.iy0 - h.fy0) + (h.fy1 - h.iy1)) * ipl : 0;
-    info->interior_nodes = fr ? Lx * Ly * ipl + info->fused_upml_nodes + info->fused_ygraded_nodes : 0;
+    info->interior_nodes = (Lx > 0 && Ly > 0 && Lz > 0) ? Lx * Ly * Lz : 0;
+    info->fused_upml_nodes = info->interior_nodes > 0 ? Lx * Ly * (c->zplanes[0] + c->zplanes[1]) : 0;
     long long sn = 0, sa = 0;
     for (int s = 0; s < h.n_slab; ++s) {
         sn += h.slab[s].n;

@@ -113,16 +113,6 @@ struct Board {
     float *zD[2];                 // [box]         D~z
     float *zB[2][2];              // [box][parity] B~z
     int zpitch;                   // row pitch of the z-UPML boxes (multiple of 8)
-    // The y-UPML rows of the interior planes [iz0, iz1) (sigma_y alone),
-    // [fy0, iy0) and [iy1, fy1), are worked by the y-face launch of the fused
-    // kernel; their B~y (ping-pong) and D~y live in two boxes (0: rows
-    // [fy0, iy0), 1: rows [iy1, fy1)); element (i, j, k) of box b at
-    // ((k - iz0) * yrows[b] + j - yj0[b]) * ypitch + i - ycol0.
-    int fy0, fy1;
-    int ypitch, ycol0;
-    int yrows[2], yj0[2];
-    float *yD[2];                 // [box]         D~y
-    float *yB[2][2];              // [box][parity] B~y
     int tm_tx, tm_ty;             // tile shape the tensor maps were encoded for
     const CUtensorMap *tm;        // kNumMaps TMA descriptors (see tm_* below)
     int n_slab;
@@ -164,12 +154,11 @@ struct Plan {
     Board *const *boards;         // [nb] device pointers
     const long long *int_prefix;  // [nb + 1] interior-kernel items (planes [iz0, iz1))
     const long long *zp_prefix;   // [nb + 1] z-UPML-kernel items (planes [1, iz0) and [iz1, nz))
-    const long long *yg_prefix;   // [nb + 1] y-face-kernel items (y-UPML rows of planes [iz0, iz1))
     const long long *slab_prefix; // [nb + 1] slab blocks
     const SlabBlock *slab_blk;    // [n_slab] per-block descriptors
     const long long *dft_prefix;  // [nb + 1] DFT warps
-    long long n_int, n_zp, n_yg, n_slab, n_dft;
-    int *work;                    // fused-kernel work counters [interior, z-UPML, y-face] (zeroed before every launch)
+    long long n_int, n_zp, n_slab, n_dft;
+    int *work;                    // fused-kernel work counters [interior, z-UPML] (zeroed before every launch)
 };
 
 // TMA descriptor slots of a board (3D maps: x, y, plane).
@@ -202,9 +191,7 @@ constexpr int kSlabThreads = 256;
 constexpr int kSlabKz = 8;          // planes per slab-kernel thread
 constexpr int kDftProbeGroup = 4;
 
-enum Phase : int {
-    kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseYFace = 2, kPhaseInterior = 3, kPhaseSlabE = 4, kPhasePost = 5, kNumPhases = 6
-};
+enum Phase : int { kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseInterior = 2, kPhaseSlabE = 3, kPhasePost = 4, kNumPhases = 5 };
 
 // Launchers (fdtd_kernels.cu).  All enqueue on `st`.
 cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cudaStream_t st);

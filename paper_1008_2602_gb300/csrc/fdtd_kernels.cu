@@ -300,7 +300,7 @@ struct Stage {
     static constexpr int BYTES = A_OFF + (ZP ? (B_CS + D_CS) * 4 : 0);
 };
 
-template <typename T, int TY, int W, int NS, bool ZP, int R, bool YG = false>
+template <typename T, int TY, int W, int NS, bool ZP, int R>
 struct FusedLayout {
     using St = Stage<T, TY, W, ZP>;
     static constexpr int BAR_OFF = NS * St::BYTES;
@@ -308,10 +308,8 @@ struct FusedLayout {
     // blocks per SM that shared memory allows (227 KB usable per SM, 1 KB
     // reserved per block); the register budget keeps them resident but never
     // drops below a per-thread floor that the warp's row count sets: 176 for
-    // 8 rows, 168 (z-UPML, y-UPML rows) or 128 for 4 rows, 136 (z-UPML, y-UPML
-    // rows) or 96 for 2 rows
-    static constexpr bool HEAVY = ZP || YG;
-    static constexpr int REG_FLOOR = TY / R >= 8 ? 176 : (TY / R >= 4 ? (HEAVY ? 168 : 128) : (HEAVY ? 136 : 96));
+    // 8 rows, 168 (z-UPML) or 128 for 4 rows, 136 (z-UPML) or 96 for 2 rows
+    static constexpr int REG_FLOOR = TY / R >= 8 ? 176 : (TY / R >= 4 ? (ZP ? 168 : 128) : (ZP ? 136 : 96));
     static constexpr int PER_SM = 232448 / (BYTES + 1024);
     static constexpr int REG_SM = 65536 / (REG_FLOOR * (32 * W * R + 32));
     static constexpr int CAP = PER_SM < REG_SM ? PER_SM : REG_SM;
@@ -328,7 +326,6 @@ struct Tile {
     const Board *B;
     int ok;
     int i0, j0, kb, ke, kstart, par;
-    int jend;                     // rows [j0, jend) of the tile are stored by this launch
 };
 
 // Items of one board: x tiles fastest, then y tiles, then z segments.  The
@@ -336,14 +333,12 @@ struct Tile {
 // covers [1, iz0) and [max(iz1, iz0), nz).  kstart is the plane below the
 // segment when the tile recomputes its H~ there, else kb (that plane's H~ is
 // then read from the output: an outer plane, or a z-UPML plane written by the
-// z-UPML launch, which runs first).  Rows: the z-UPML and interior launches
-// cover [iy0, iy1); the y-face launch (YG) covers the y-UPML rows of the
-// interior planes, [fy0, iy0) then [iy1, fy1), each face tiled on its own.
-template <int TY, int W, bool ZP, bool YG = false>
+// z-UPML launch, which runs first).
+template <int TY, int W, bool ZP>
 __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 {
     Tile t;
-    const long long *prefix = ZP ? plan.zp_prefix : (YG ? plan.yg_prefix : plan.int_prefix);
+    const long long *prefix = ZP ? plan.zp_prefix : plan.int_prefix;
     const int b = find_board(prefix, plan.nb, item);
     t.B = plan.boards[b];
     // a board whose tensor maps were encoded for another tile is skipped (its
@@ -353,24 +348,12 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
     t.par = (int)(step & 1);
     const long long local = item - __ldg(prefix + b);
     constexpr int TX = kWarpCols * W;
-    const int iy0 = t.B->iy0, iy1 = t.B->iy1;
-    const int nlow = YG ? (iy0 - t.B->fy0 + TY - 1) / TY : 0;   // tile rows of the low y face
-    const int ntx = (t.B->ix1 - t.B->ix0 + TX - 1) / TX;
-    const int nty = YG ? nlow + (t.B->fy1 - iy1 + TY - 1) / TY : (iy1 - iy0 + TY - 1) / TY;
+    const int ntx = (t.B->ix1 - t.B->ix0 + TX - 1) / TX, nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
     const int tx = (int)(local % ntx);
     const long long rest = local / ntx;
     const int ty = (int)(rest % nty), tz = (int)(rest / nty);
     t.i0 = t.B->ix0 + tx * TX;
-    if (!YG) {
-        t.j0 = iy0 + ty * TY;
-        t.jend = iy1;
-    } else if (ty < nlow) {
-        t.j0 = t.B->fy0 + ty * TY;
-        t.jend = iy0;
-    } else {
-        t.j0 = iy1 + (ty - nlow) * TY;
-        t.jend = t.B->fy1;
-    }
+    t.j0 = t.B->iy0 + ty * TY;
     const int zs = plan.zseg, iz0 = t.B->iz0, iz1 = t.B->iz1;
     if (!ZP) {
         t.kb = iz0 + tz * zs;
@@ -410,11 +393,11 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
 // only.  In z-UPML planes (sigma_z only) H~z carries B~z and E_z carries
 // D~z, while H~x, H~y, E_x, E_y update in the lossy form; those planes use
 // the scalar update helpers per element, every other plane the paired form.
-template <typename T, int TY, int W, int NS, bool ZP, int R, bool YG>
-__global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP, R, YG>::MINB)) k_fused(Plan plan)
+template <typename T, int TY, int W, int NS, bool ZP, int R>
+__global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP, R>::MINB)) k_fused(Plan plan)
 {
     using St = Stage<T, TY, W, ZP>;
-    using L = FusedLayout<T, TY, W, NS, ZP, R, YG>;
+    using L = FusedLayout<T, TY, W, NS, ZP, R>;
     constexpr int TYW = TY / R;   // rows of one compute warp
     static_assert(TY % R == 0, "row groups must split the tile evenly");
     extern __shared__ __align__(128) unsigned char smem[];
@@ -447,11 +430,11 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
                 eph ^= 1u << s;
             }
         };
-        const long long n_items = ZP ? plan.n_zp : (YG ? plan.n_yg : plan.n_int);
+        const long long n_items = ZP ? plan.n_zp : plan.n_int;
         for (;;) {
-            const long long item = atomicAdd(plan.work + (ZP ? 1 : (YG ? 2 : 0)), 1);
+            const long long item = atomicAdd(plan.work + (ZP ? 1 : 0), 1);
             if (item >= n_items) break;
-            const Tile t = decode_tile<TY, W, ZP, YG>(plan, item);
+            const Tile t = decode_tile<TY, W, ZP>(plan, item);
             const Board *B = t.B;
             if (!t.ok && (B->tm_tx != kWarpCols * W || B->tm_ty != TY)) atomicOr(B->status, 4);
             const CUtensorMap *tm = B->tm;
@@ -503,7 +486,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
         mbar_wait(&full[sq], (fph >> sq) & 1u, plan.boards[0]->status, abort_flag);
         const long long item = *reinterpret_cast<volatile long long *>(smem + sq * St::BYTES + St::ITEM_OFF);
         if (item < 0) break;   // -1: no more work (the stage is left full)
-        const Tile t = decode_tile<TY, W, ZP, YG>(plan, item);
+        const Tile t = decode_tile<TY, W, ZP>(plan, item);
         if (!t.ok) {           // one empty plane was sent for an inactive board
             fph ^= 1u << sq;
             __syncwarp();
@@ -534,14 +517,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
         const int ecol = (g - ((i0 - 1) & ~7)) + 2 * lx;   // column of ca in the E/H boxes (even)
         const int xc0 = id16 ? (i0 & ~7) : (i0 & ~15);
         const int ida = max(ca - xc0, 0), idb = cb - xc0;  // columns in the id box (clamped into it)
-        const int fy1 = t.jend;                       // rows stored by this launch end here
-        const bool row_zero = YG && jb == 0;          // row -1 lies behind the PEC wall: its H~ image is 0
-        // row jb-1 read from the output: written by the slab kernels (or, for
-        // the interior launch's row iy0-1, by the y-face launch, which runs first)
-        const bool row_slab = !row_zero && jb - 1 < (YG ? B->fy0 : iy0);
-        // y-UPML rows of the y-face launch: B~y (ping-pong) and D~y boxes
-        const int ypitch = YG ? B->ypitch : 0;
-        const bool yaux_lane = YG && cb >= ix0 && ca < ix1;   // the lane's pair lies in the boxes' columns
+        const bool row_slab = (jb - 1 < iy0);
         // element (ca, jb-1, kstart) of component 0 in the output parity, advanced by P per plane
         T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(jb - 1) * X + ca);
         const int zrow = B->zpitch;
@@ -556,7 +532,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
         if (kstart == kb) {         // plane kb-1 is not recomputed: read its H~
 #pragma unroll
             for (int r = 0; r < TYW; ++r)
-                if (jb + r < fy1) {
+                if (jb + r < iy1) {
                     const T *gq = gp - P + (long long)(r + 1) * X;
                     if (own_a) { hk1x[r].x = Io<T>::ld(gq + 3 * NN); hk1y[r].x = Io<T>::ld(gq + 4 * NN); }
                     if (own_b) { hk1x[r].y = Io<T>::ld(gq + 3 * NN + 1); hk1y[r].y = Io<T>::ld(gq + 4 * NN + 1); }
@@ -615,30 +591,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
                 const float2 scz = curl2v(eyx, ey, exu, ex, Sx2, nSy2);
                 const float2 ohx = Pair<T>::lds(H0 + rr * HW), ohy = Pair<T>::lds(H0 + HCS + rr * HW);
                 const float2 ohz = Pair<T>::lds(H0 + 2 * HCS + rr * HW);
-                const int jr = jb - 1 + rr;   // grid row
-                if (YG && jr < fy1 && (jr < iy0 || jr >= iy1)) {
-                    // y-UPML row (sigma_y alone): H~x, H~z in the lossy form with
-                    // the y factors at j+1/2; H~y through B~y with those at j
-                    const Coef yh = B->cw[1][1][jr], yi = B->cw[1][0][jr];
-                    const float2 b1 = make_float2(yh.b1, yh.b1), ng = make_float2(-yh.g, -yh.g);
-                    hx = __ffma2_rn(ng, scx, __fmul2_rn(b1, ohx));
-                    hz = __ffma2_rn(ng, scz, __fmul2_rn(b1, ohz));
-                    const int ybx = jr < iy0 ? 0 : 1;
-                    const long long ya =
-                        ((long long)(k - iz0) * B->yrows[ybx] + (jr - B->yj0[ybx])) * ypitch + (ca - B->ycol0);
-                    float2 bo = make_float2(0.f, 0.f);
-                    if (yaux_lane) bo = __ldg(reinterpret_cast<const float2 *>(B->yB[ybx][par] + ya));
-                    const float2 bn = sub2(bo, scy);
-                    hy = __ffma2_rn(make_float2(1.0f, 1.0f),
-                                    __ffma2_rn(make_float2(yi.ap, yi.ap), bn, __fmul2_rn(make_float2(-yi.am, -yi.am), bo)),
-                                    ohy);
-                    if (rr >= 1 && full_plane) {   // an owned row of a stored plane: B~y to the other parity
-                        float *ybn = B->yB[ybx][par ^ 1] + ya;
-                        if (own_a && own_b) stg2(ybn, bn);
-                        else if (own_a) stg1(ybn, bn.x);
-                        else if (own_b) stg1(ybn + 1, bn.y);
-                    }
-                } else if (!ZP || !zb) {
+                if (!ZP || !zb) {
                     hx = sub2(ohx, scx);
                     hy = sub2(ohy, scy);
                     hz = sub2(ohz, scz);
@@ -656,7 +609,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
             };
             // halo elements outside the fused region come from the slab output
             auto slab_fix = [&](int rr, float2 &hx, float2 &hy, float2 &hz) {
-                if (jb - 1 + rr >= fy1) return;
+                if (jb - 1 + rr >= iy1) return;
                 const T *gq = gp + (long long)rr * X;
                 if (slab_a) { hx.x = Io<T>::ld(gq + 3 * NN); hy.x = Io<T>::ld(gq + 4 * NN); hz.x = Io<T>::ld(gq + 5 * NN); }
                 if (slab_b) {
@@ -665,7 +618,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
             };
 
             float2 px = make_float2(0.f, 0.f), pz = px;   // H~x, H~z at (., j-1)
-            if (full_plane && !row_zero) {
+            if (full_plane) {
                 if (row_slab) {   // row jb-1 lies in the low-y slab: read its H~ (own columns)
                     if (own_a && own_b) {
                         px = Pair<T>::ldg(gp + 3 * NN);
@@ -691,36 +644,14 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
                 slab_fix(rr, hx, hy, hz);
                 const float hyl = __shfl_up_sync(0xffffffffu, hy.y, 1);   // H~ at (ca-1, j)
                 const float hzl = __shfl_up_sync(0xffffffffu, hz.y, 1);
-                if (full_plane && j < fy1) {
+                if (full_plane && j < iy1) {
                     const float2 hym = make_float2(hyl, hy.x), hzm = make_float2(hzl, hz.x);   // H~ at (c-1, j)
                     const float2 scx = curl2v(hz, pz, hy, hk1y[r], Sy2, nSz2);
                     const float2 scy = curl2v(hx, hk1x[r], hz, hzm, Sz2, nSx2);
                     const float2 scz = curl2v(hy, hym, hx, px, Sx2, nSy2);
                     float2 exv, eyv, ezv;
                     T *o = gp + (long long)rr * X;
-                    if (YG && (j < iy0 || j >= iy1)) {
-                        // y-UPML row: E_x, E_z in the lossy form with the y factors
-                        // at j; E_y through D~y with those at j+1/2 (updated in
-                        // place); B~y of the row goes to the other parity
-                        const Coef yi = B->cw[1][0][j], yh = B->cw[1][1][j];
-                        const int ybx = j < iy0 ? 0 : 1;
-                        const long long ya =
-                            ((long long)(k - iz0) * B->yrows[ybx] + (j - B->yj0[ybx])) * ypitch + (ca - B->ycol0);
-                        exv = make_float2(__fmaf_rn(__fmul_rn(cea[r].x, yi.g), scx.x, __fmul_rn(yi.b1, ex.x)),
-                                          __fmaf_rn(__fmul_rn(ceb[r].x, yi.g), scx.y, __fmul_rn(yi.b1, ex.y)));
-                        ezv = make_float2(__fmaf_rn(__fmul_rn(cea[r].z, yi.g), scz.x, __fmul_rn(yi.b1, ez.x)),
-                                          __fmaf_rn(__fmul_rn(ceb[r].z, yi.g), scz.y, __fmul_rn(yi.b1, ez.y)));
-                        float *yd = B->yD[ybx] + ya;
-                        float2 dold = make_float2(0.f, 0.f);
-                        if (yaux_lane) dold = *reinterpret_cast<const float2 *>(yd);
-                        const float2 dn = __ffma2_rn(make_float2(1.0f, 1.0f), scy, dold);
-                        const float2 xd =
-                            __ffma2_rn(make_float2(yh.ap, yh.ap), dn, __fmul2_rn(make_float2(-yh.am, -yh.am), dold));
-                        eyv = make_float2(__fmaf_rn(cea[r].y, xd.x, ey.x), __fmaf_rn(ceb[r].y, xd.y, ey.y));
-                        if (own_a && own_b) stg2(yd, dn);
-                        else if (own_a) stg1(yd, dn.x);
-                        else if (own_b) stg1(yd + 1, dn.y);
-                    } else if (!ZP || !zb) {
+                    if (!ZP || !zb) {
                         exv = make_float2(__fmaf_rn(cea[r].x, scx.x, ex.x), __fmaf_rn(ceb[r].x, scx.y, ex.y));
                         eyv = make_float2(__fmaf_rn(cea[r].y, scy.x, ey.x), __fmaf_rn(ceb[r].y, scy.y, ey.y));
                         ezv = make_float2(__fmaf_rn(cea[r].z, scz.x, ez.x), __fmaf_rn(ceb[r].z, scz.y, ez.y));
@@ -1388,10 +1319,10 @@ cudaError_t launch_wait_selftest(int *status, unsigned max_polls, cudaStream_t s
 // NS-stage ring; ZP selects the z-UPML launch.
 constexpr int kFusedStages = 3;
 
-template <typename T, int TY, int W, bool ZP, int R, bool YG = false>
+template <typename T, int TY, int W, bool ZP, int R>
 struct FusedCfg {
     static constexpr int NS = kFusedStages;
-    using L = FusedLayout<T, TY, W, NS, ZP, R, YG>;
+    using L = FusedLayout<T, TY, W, NS, ZP, R>;
     static dim3 block() { return dim3(32, W * R + 1); }
     static int grid()
     {
@@ -1400,7 +1331,7 @@ struct FusedCfg {
             int dev = 0, sms = 0, per = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS, ZP, R, YG>, 32 * (W * R + 1),
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_fused<T, TY, W, NS, ZP, R>, 32 * (W * R + 1),
                                                           L::BYTES);
             g = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
         }
@@ -1408,30 +1339,30 @@ struct FusedCfg {
     }
     static cudaError_t set_limit()
     {
-        return cudaFuncSetAttribute(k_fused<T, TY, W, NS, ZP, R, YG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        return cudaFuncSetAttribute(k_fused<T, TY, W, NS, ZP, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     L::BYTES);
     }
     static void launch(const Plan &plan, cudaStream_t st)
     {
-        const long long n = ZP ? plan.n_zp : (YG ? plan.n_yg : plan.n_int);
+        const long long n = ZP ? plan.n_zp : plan.n_int;
         if (n <= 0) return;
         const int g = (int)(n < grid() ? n : grid());
-        k_fused<T, TY, W, NS, ZP, R, YG><<<g, block(), L::BYTES, st>>>(plan);
+        k_fused<T, TY, W, NS, ZP, R><<<g, block(), L::BYTES, st>>>(plan);
     }
 };
 
 // Supported fused tiles (tile_x columns x tile_y rows): 62x4 and 124x4 (one
 // compute warp per 62 columns), 62x8 (four compute warps of two rows sharing
 // the stage) and 124x8 (two compute warps of four rows per 62 columns).
-template <typename T, bool ZP, bool YG = false>
+template <typename T, bool ZP>
 static void launch_fused(const Plan &plan, cudaStream_t st)
 {
     const int key = plan.tile_x * 16 + plan.tile_y;
     switch (key) {
-    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP, 4, YG>::launch(plan, st); break;
-    case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP, 1, YG>::launch(plan, st); break;
-    case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP, 2, YG>::launch(plan, st); break;
-    default: FusedCfg<T, 4, 1, ZP, 1, YG>::launch(plan, st); break;
+    case 62 * 16 + 8: FusedCfg<T, 8, 1, ZP, 4>::launch(plan, st); break;
+    case 124 * 16 + 4: FusedCfg<T, 4, 2, ZP, 1>::launch(plan, st); break;
+    case 124 * 16 + 8: FusedCfg<T, 8, 2, ZP, 2>::launch(plan, st); break;
+    default: FusedCfg<T, 4, 1, ZP, 1>::launch(plan, st); break;
     }
 }
 
@@ -1450,12 +1381,6 @@ static cudaError_t phase_t(const Plan &plan, int phase, int grid_cap, cudaStream
         if (plan.n_zp > 0) {
             cudaMemsetAsync(plan.work + 1, 0, sizeof(int), st);
             launch_fused<T, true>(plan, st);
-        }
-        break;
-    case kPhaseYFace:
-        if (plan.n_yg > 0) {
-            cudaMemsetAsync(plan.work + 2, 0, sizeof(int), st);
-            launch_fused<T, false, true>(plan, st);
         }
         break;
     case kPhaseInterior:
@@ -1497,14 +1422,12 @@ bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (t
 template <typename T>
 static cudaError_t limits_t()
 {
-    cudaError_t e[14] = {cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
+    cudaError_t e[10] = {cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
                          cudaFuncSetAttribute(k_slab_e<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabESmem),
                          FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 4>::set_limit(),
                          FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),
                          FusedCfg<T, 4, 1, true, 1>::set_limit(),  FusedCfg<T, 8, 1, true, 4>::set_limit(),
-                         FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit(),
-                         FusedCfg<T, 4, 1, false, 1, true>::set_limit(), FusedCfg<T, 8, 1, false, 4, true>::set_limit(),
-                         FusedCfg<T, 4, 2, false, 1, true>::set_limit(), FusedCfg<T, 8, 2, false, 2, true>::set_limit()};
+                         FusedCfg<T, 4, 2, true, 1>::set_limit(),  FusedCfg<T, 8, 2, true, 2>::set_limit()};
     for (cudaError_t x : e)
         if (x != cudaSuccess) return x;
     return cudaSuccess;

@@ -70,9 +70,9 @@ class Solver:
 
     def step_profiled(self, n: int) -> np.ndarray:
         """n steps with per-phase CUDA-event timing: [slab H, fused z-UPML,
-        fused y-UPML rows, fused interior, slab E, sources/probes, DFT]
-        summed device milliseconds."""
-        ms = (ctypes.c_double * 7)()
+        fused interior, slab E, sources/probes, DFT] summed device
+        milliseconds."""
+        ms = (ctypes.c_double * 6)()
         C.fdtd_step_profiled(self.ctx, int(n), ms)
         return np.array(list(ms))
 
