@@ -75,6 +75,8 @@ _SIGS = {
     "fdtd_node_coefficients": (c_int, [P(fdtd_grid), c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                        P(fdtd_boundary), c_void_p, c_void_p, c_int, P(c_int)]),
     "fdtd_info": (c_int, [c_void_p, P(fdtd_info_t)]),
+    "fdtd_device_bytes": (c_int, [P(fdtd_grid), P(fdtd_boundary), c_int, c_int, c_int, c_int, c_double,
+                                  P(c_longlong)]),
     "fdtd_save": (c_int, [c_void_p, c_void_p, ctypes.c_size_t, P(ctypes.c_size_t)]),
     "fdtd_selftest_wait_timeout": (c_int, [c_void_p, ctypes.c_uint]),
     "fdtd_load": (c_int, [c_void_p, c_void_p, ctypes.c_size_t]),

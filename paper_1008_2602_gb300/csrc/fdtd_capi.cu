@@ -189,21 +189,129 @@ struct Axes {
     std::vector<Coef> cw[3][2];   // [axis][int/half][0..N]
 };
 
-void build_axes(const fdtd_ctx *c, Axes &A)
+void build_axes(const fdtd_grid &g, const fdtd_boundary &bnd, double dt, Axes &A)
 {
-    const int N[3] = {c->g.nx, c->g.ny, c->g.nz};
-    const double D[3] = {c->g.dx, c->g.dy, c->g.dz};
+    const int N[3] = {g.nx, g.ny, g.nz};
+    const double D[3] = {g.dx, g.dy, g.dz};
     for (int w = 0; w < 3; ++w) {
-        const int dlo = c->bnd.depth[2 * w], dhi = c->bnd.depth[2 * w + 1];
+        const int dlo = bnd.depth[2 * w], dhi = bnd.depth[2 * w + 1];
         A.cw[w][0].resize(N[w] + 1);
         A.cw[w][1].resize(N[w] + 1);
         for (int i = 0; i <= N[w]; ++i) {
-            A.cw[w][0][i] = upml_coef((double)i, N[w], dlo, dhi, D[w], c->bnd.m, c->bnd.R0, c->bnd.kappa_max, c->dt);
-            A.cw[w][1][i] = i < N[w] ? upml_coef(i + 0.5, N[w], dlo, dhi, D[w], c->bnd.m, c->bnd.R0,
-                                                 c->bnd.kappa_max, c->dt)
+            A.cw[w][0][i] = upml_coef((double)i, N[w], dlo, dhi, D[w], bnd.m, bnd.R0, bnd.kappa_max, dt);
+            A.cw[w][1][i] = i < N[w] ? upml_coef(i + 0.5, N[w], dlo, dhi, D[w], bnd.m, bnd.R0, bnd.kappa_max, dt)
                                      : Coef{1.0f, 1.0f, 1.0f, 1.0f};
         }
     }
+}
+void build_axes(const fdtd_ctx *c, Axes &A) { build_axes(c->g, c->bnd, c->dt, A); }
+
+double grid_dt(const fdtd_grid &g)
+{
+    return g.dt > 0 ? g.dt : g.courant / (kC0 * std::sqrt(1.0 / (g.dx * g.dx) + 1.0 / (g.dy * g.dy) + 1.0 / (g.dz * g.dz)));
+}
+
+// Fused region and slab boxes of a board (host only): sets the region's
+// bounds, the slab boxes with their thread blocks, the z-UPML box planes and
+// pitch in h, and which of the six auxiliaries each box keeps in aux.
+// Returns false if the boxes exceed kMaxSlab.
+bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, Board &h, bool aux[kMaxSlab][6],
+                  long long zplanes[2])
+{
+    const int nx = g.nx, ny = g.ny, nz = g.nz;
+    // fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) and the slabs around it
+    h.ix0 = std::max(bnd.depth[0], 1); h.ix1 = nx - bnd.depth[1];
+    h.iy0 = std::max(bnd.depth[2], 1); h.iy1 = ny - bnd.depth[3];
+    h.iz0 = std::max(bnd.depth[4], 1); h.iz1 = nz - bnd.depth[5];
+    std::vector<std::array<int, 6>> boxes;
+    const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
+    if (!fused) {
+        h.ix0 = h.ix1 = h.iy0 = h.iy1 = 0;
+        h.iz0 = 1; h.iz1 = nz;
+        boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
+    } else {
+        // The slabs are split where the set of graded axes changes, so that each
+        // box carries only the auxiliaries its own nodes need: faces graded
+        // along one axis keep two, edges and corners six.  Per axis the node
+        // ranges are low UPML, middle and high UPML; the z ranges of the
+        // outer boxes include the wall plane k = 0.
+        // A high wall plane (i = nx, j = ny or k = nz) behind a PEC wall holds
+        // no unknown: its tangential E edges are PEC, the normal H on it sees
+        // the curl of those zero edges, and the other samples do not exist.
+        // Everything there stays zero, so those planes are left out of the
+        // boxes (their zeros are still read as neighbours).  The low wall
+        // planes keep the H and E samples half a cell inside.
+        const int xe = bnd.wall[1] == FDTD_WALL_PEC ? nx : nx + 1;
+        const int ye = bnd.wall[3] == FDTD_WALL_PEC ? ny : ny + 1;
+        const int ze = bnd.wall[5] == FDTD_WALL_PEC ? nz : nz + 1;
+        const int xs[4] = {0, h.ix0, h.ix1, xe}, ys[4] = {0, h.iy0, h.iy1, ye};
+        const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), ze};
+        for (int zb = 0; zb < 3; zb += 2) {
+            // z-UPML layers with the wall plane: y strips cut where the x
+            // grading starts (each piece then keeps only the auxiliaries of
+            // its own graded axes: on a sub-board whose y face is a cut, not
+            // a UPML, the middle is a plain z face), then x strips
+            for (int yb = 0; yb < 3; yb += 2)
+                for (int xb = 0; xb < 3; ++xb) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
+            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
+            // the wall plane of the interior columns (the fused kernels start at k = 1)
+            const int kw = zb == 0 ? 0 : nz;
+            if (kw < ze) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
+        }
+        // planes between the z-UPML layers: y faces, x faces, the four corner columns
+        for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});
+        for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[1], zs[2]});
+        for (int yb = 0; yb < 3; yb += 2)
+            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[1], zs[2]});
+    }
+    if ((int)boxes.size() > kMaxSlab) return false;
+    h.n_slab = 0;
+    int blocks = 0;
+    for (const auto &bx : boxes) {
+        if (bx[1] <= bx[0] || bx[3] <= bx[2] || bx[5] <= bx[4]) continue;
+        Slab &sl = h.slab[h.n_slab];
+        sl.i0 = bx[0]; sl.i1 = bx[1]; sl.j0 = bx[2]; sl.j1 = bx[3]; sl.k0 = bx[4]; sl.k1 = bx[5];
+        sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
+        sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
+        sl.block0 = blocks;
+        // threads: (i, j) columns marching z, or (i, k) columns marching y for a single plane
+        const long long cols = sl.k1 - sl.k0 == 1 ? (long long)sl.ni * ((sl.nj + kSlabKz - 1) / kSlabKz)
+                                                  : (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
+        blocks += (int)((cols + kSlabThreads - 1) / kSlabThreads);
+        const int lo[3] = {sl.i0, sl.j0, sl.k0}, hi[3] = {sl.i1, sl.j1, sl.k1};
+        auto any_nontrivial = [&](int axis, int half, bool need_b1g, bool need_apam) {
+            for (int t = lo[axis]; t < hi[axis]; ++t) {
+                const Coef &cf = A.cw[axis][half][t];
+                if (need_b1g && (cf.b1 != 1.0f || cf.g != 1.0f)) return true;
+                if (need_apam && (cf.ap != 1.0f || cf.am != 1.0f)) return true;
+            }
+            return false;
+        };
+        for (int comp = 0; comp < 6; ++comp) {
+            const int w = comp % 3, w1 = (w + 1) % 3, w2 = (w + 2) % 3;
+            const bool is_h = comp >= 3;
+            // E: D recurrence along w1, E recurrence along w2 (integer), D->E along w (half)
+            // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
+            // An auxiliary is needed where D->E (B->H) is graded or both
+            // recurrences are; otherwise the lossy form holds exactly (also
+            // with FP16 field storage, whose 11-bit mantissa keeps the
+            // per-step UPML decay applied to the stored value within the
+            // storage mode's error target).
+            const int rec = is_h ? 1 : 0;
+            aux[h.n_slab][comp] = any_nontrivial(w, is_h ? 0 : 1, false, true) ||
+                                  (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
+            sl.aux[comp] = nullptr;
+        }
+        ++h.n_slab;
+    }
+    h.slab_blocks = blocks;
+    // z-UPML boxes of the fused region: lower planes [1, iz0), upper [iz1, nz)
+    h.zpitch = fused ? ((h.ix1 - h.ix0) + 7) & ~7 : 0;
+    for (int bx = 0; bx < 2; ++bx) {
+        const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
+        zplanes[bx] = fused && planes > 0 ? planes : 0;
+    }
+    return true;
 }
 
 // Per-node coefficient ids: ce = 1/eps_r(edge) for the three edges starting at
@@ -922,105 +1030,22 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         }
     if (r) { fdtd_destroy(c); return r; }
 
-    // fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) and the slabs around it
-    const int nx = grid->nx, ny = grid->ny, nz = grid->nz;
-    h.ix0 = std::max(bnd->depth[0], 1); h.ix1 = nx - bnd->depth[1];
-    h.iy0 = std::max(bnd->depth[2], 1); h.iy1 = ny - bnd->depth[3];
-    h.iz0 = std::max(bnd->depth[4], 1); h.iz1 = nz - bnd->depth[5];
-    std::vector<std::array<int, 6>> boxes;
-    const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
-    if (!fused) {
-        h.ix0 = h.ix1 = h.iy0 = h.iy1 = 0;
-        h.iz0 = 1; h.iz1 = nz;
-        boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
-    } else {
-        // The slabs are split where the set of graded axes changes, so that each
-        // box carries only the auxiliaries its own nodes need: faces graded
-        // along one axis keep two, edges and corners six.  Per axis the node
-        // ranges are low UPML, middle and high UPML; the z ranges of the
-        // outer boxes include the wall plane k = 0.
-        // A high wall plane (i = nx, j = ny or k = nz) behind a PEC wall holds
-        // no unknown: its tangential E edges are PEC, the normal H on it sees
-        // the curl of those zero edges, and the other samples do not exist.
-        // Everything there stays zero, so those planes are left out of the
-        // boxes (their zeros are still read as neighbours).  The low wall
-        // planes keep the H and E samples half a cell inside.
-        const int xe = bnd->wall[1] == FDTD_WALL_PEC ? nx : nx + 1;
-        const int ye = bnd->wall[3] == FDTD_WALL_PEC ? ny : ny + 1;
-        const int ze = bnd->wall[5] == FDTD_WALL_PEC ? nz : nz + 1;
-        const int xs[4] = {0, h.ix0, h.ix1, xe}, ys[4] = {0, h.iy0, h.iy1, ye};
-        const int zs[4] = {0, h.iz0, std::max(h.iz1, h.iz0), ze};
-        for (int zb = 0; zb < 3; zb += 2) {
-            // z-UPML layers with the wall plane: y strips cut where the x
-            // grading starts (each piece then keeps only the auxiliaries of
-            // its own graded axes: on a sub-board whose y face is a cut, not
-            // a UPML, the middle is a plain z face), then x strips
-            for (int yb = 0; yb < 3; yb += 2)
-                for (int xb = 0; xb < 3; ++xb) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
-            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
-            // the wall plane of the interior columns (the fused kernels start at k = 1)
-            const int kw = zb == 0 ? 0 : nz;
-            if (kw < ze) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
-        }
-        // planes between the z-UPML layers: y faces, x faces, the four corner columns
-        for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});
-        for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[1], zs[2]});
-        for (int yb = 0; yb < 3; yb += 2)
-            for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[1], zs[2]});
-    }
-    if ((int)boxes.size() > kMaxSlab) { fdtd_destroy(c); return fail(FDTD_EINVAL, "internal: too many slab boxes"); }
-    h.n_slab = 0;
-    int blocks = 0;
-    for (const auto &bx : boxes) {
-        if (bx[1] <= bx[0] || bx[3] <= bx[2] || bx[5] <= bx[4]) continue;
-        Slab &sl = h.slab[h.n_slab++];
-        sl.i0 = bx[0]; sl.i1 = bx[1]; sl.j0 = bx[2]; sl.j1 = bx[3]; sl.k0 = bx[4]; sl.k1 = bx[5];
-        sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
-        sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
-        sl.block0 = blocks;
-        // threads: (i, j) columns marching z, or (i, k) columns marching y for a single plane
-        const long long cols = sl.k1 - sl.k0 == 1 ? (long long)sl.ni * ((sl.nj + kSlabKz - 1) / kSlabKz)
-                                                  : (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
-        blocks += (int)((cols + kSlabThreads - 1) / kSlabThreads);
-        const int lo[3] = {sl.i0, sl.j0, sl.k0}, hi[3] = {sl.i1, sl.j1, sl.k1};
-        auto any_nontrivial = [&](int axis, int half, bool need_b1g, bool need_apam) {
-            for (int t = lo[axis]; t < hi[axis]; ++t) {
-                const Coef &cf = A.cw[axis][half][t];
-                if (need_b1g && (cf.b1 != 1.0f || cf.g != 1.0f)) return true;
-                if (need_apam && (cf.ap != 1.0f || cf.am != 1.0f)) return true;
-            }
-            return false;
-        };
-        for (int comp = 0; comp < 6; ++comp) {
-            const int w = comp % 3, w1 = (w + 1) % 3, w2 = (w + 2) % 3;
-            const bool is_h = comp >= 3;
-            // E: D recurrence along w1, E recurrence along w2 (integer), D->E along w (half)
-            // H: B recurrence along w1, H recurrence along w2 (half),    B->H along w (integer)
-            // An auxiliary is needed where D->E (B->H) is graded or both
-            // recurrences are; otherwise the lossy form holds exactly (also
-            // with FP16 field storage, whose 11-bit mantissa keeps the
-            // per-step UPML decay applied to the stored value within the
-            // storage mode's error target).
-            const int rec = is_h ? 1 : 0;
-            const bool need = any_nontrivial(w, is_h ? 0 : 1, false, true) ||
-                              (any_nontrivial(w1, rec, true, false) && any_nontrivial(w2, rec, true, false));
-            sl.aux[comp] = nullptr;
-            if (need && !r) {
-                r = dalloc(c, &sl.aux[comp], sizeof(float) * (size_t)sl.n);
-                if (!r) { cudaError_t e = cudaMemsetAsync(sl.aux[comp], 0, sizeof(float) * (size_t)sl.n, c->cur); if (e) r = cuda_fail(e, "memset"); }
-            }
+    // fused region and slab boxes
+    bool aux[kMaxSlab][6];
+    if (!layout_board(*grid, *bnd, A, h, aux, c->zplanes)) { fdtd_destroy(c); return fail(FDTD_EINVAL, "internal: too many slab boxes"); }
+    for (int s = 0; s < h.n_slab && !r; ++s) {
+        Slab &sl = h.slab[s];
+        for (int comp = 0; comp < 6 && !r; ++comp) {
+            if (!aux[s][comp]) continue;
+            r = dalloc(c, &sl.aux[comp], sizeof(float) * (size_t)sl.n);
+            if (!r) { cudaError_t e = cudaMemsetAsync(sl.aux[comp], 0, sizeof(float) * (size_t)sl.n, c->cur); if (e) r = cuda_fail(e, "memset"); }
         }
     }
-    // z-UPML auxiliaries of the fused region: lower box planes [1, iz0), upper [iz1, nz)
     for (int bx = 0; bx < 2; ++bx) {
         h.zD[bx] = nullptr;
         h.zB[bx][0] = h.zB[bx][1] = nullptr;
-        if (!fused) continue;
-        const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
-        if (planes <= 0) continue;
-        h.zpitch = ((h.ix1 - h.ix0) + 7) & ~7;
-        const size_t n = (size_t)planes * h.zpitch * (h.iy1 - h.iy0);
-        c->zplanes[bx] = planes;
+        if (!c->zplanes[bx]) continue;
+        const size_t n = (size_t)c->zplanes[bx] * h.zpitch * (h.iy1 - h.iy0);
         float *ptr[3] = {nullptr, nullptr, nullptr};   // D~z, B~z (two parities)
         for (int t = 0; t < 3 && !r; ++t) {
             r = dalloc(c, &ptr[t], sizeof(float) * n);
@@ -1031,7 +1056,6 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
         h.zB[bx][1] = ptr[2];
         c->zaux_n[bx] = n;
     }
-    h.slab_blocks = blocks;
     long long *ctr = nullptr;
     const long long init[4] = {0, LLONG_MAX, 0, 0};
     if (!r) r = dalloc(c, &ctr, 4 * sizeof(long long));
@@ -1648,6 +1672,52 @@ int fdtd_node_coefficients(const fdtd_grid *grid, const uint8_t *mat_ids, const 
             const size_t src = ((size_t)k * NY + j) * c.h.pitch, dst = ((size_t)k * NY + j) * NX;
             for (int i = 0; i < NX; ++i) ids[dst + i] = nid.wide ? nid.cid[src + i] : (uint16_t)nid.c8[src + i];
         }
+    return FDTD_OK;
+}
+
+int fdtd_device_bytes(const fdtd_grid *grid, const fdtd_boundary *bnd, int precision, int n_sources, int n_probes,
+                      int n_total_steps, double f_max, long long *bytes)
+{
+    if (!grid || !bnd || !bytes) return fail(FDTD_EINVAL, "NULL argument");
+    if (precision != FDTD_FP32 && precision != FDTD_FP16_STORE)
+        return fail(FDTD_EINVAL, "precision must be FDTD_FP32 or FDTD_FP16_STORE");
+    if (n_sources < 0 || n_probes < 0 || n_total_steps < 0) return fail(FDTD_EINVAL, "negative count");
+    const double one = 1.0;
+    const uint8_t mat0 = 0;
+    if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(FDTD_EINVAL, "grid must have at least one cell per axis");
+    if (int r = check_problem(grid, &mat0, &one, 1, nullptr, 0, bnd)) return r;
+    const long long pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    const long long nodes = pitch * (grid->ny + 1) * (grid->nz + 1);
+    const double dt = grid_dt(*grid);
+    Axes A;
+    build_axes(*grid, *bnd, dt, A);
+    std::unique_ptr<Board> hb(new Board());
+    Board &h = *hb;
+    h.nx = grid->nx; h.ny = grid->ny; h.nz = grid->nz;
+    bool aux[kMaxSlab][6];
+    long long zplanes[2] = {0, 0};
+    if (!layout_board(*grid, *bnd, A, h, aux, zplanes)) return fail(FDTD_EINVAL, "internal: too many slab boxes");
+    auto al = [](long long b) { return b > 0 ? b : 16LL; };   // as the allocator rounds empty requests
+    long long t = 2 * al(6 * nodes * elem_size(precision));                    // both field parities
+    t += al(nodes * 2) + al((long long)sizeof(float4) * kMaxCombo16);         // 16-bit ids and their table (upper bound)
+    for (int w = 0; w < 3; ++w) t += 2 * al((long long)sizeof(Coef) * A.cw[w][0].size());   // UPML factors
+    for (int s = 0; s < h.n_slab; ++s)
+        for (int comp = 0; comp < 6; ++comp)
+            if (aux[s][comp]) t += al(4 * h.slab[s].n);
+    for (int bx = 0; bx < 2; ++bx)
+        if (zplanes[bx]) t += 3 * al(4 * zplanes[bx] * h.zpitch * (h.iy1 - h.iy0));
+    t += al(4 * sizeof(long long)) + al(sizeof(Board));
+    t += al((long long)sizeof(double) * (2 * (long long)energy_partials(h) + 2));
+    if (h.ix1 > h.ix0) t += al((long long)sizeof(CUtensorMap) * kNumMaps);
+    if (n_sources) t += al((long long)sizeof(Source) * n_sources);
+    if (n_probes) t += al((long long)sizeof(Probe) * n_probes);
+    if (n_total_steps > 0 && n_probes > 0) {
+        const int nyq = n_total_steps / 2 + 1;
+        int Q = nyq;
+        if (f_max > 0) Q = std::min(nyq, (int)std::floor(f_max * n_total_steps * dt + 1e-9) + 1);
+        t += al(4LL * n_probes * n_total_steps) + al(16LL * n_probes * std::max(Q, 1));
+    }
+    *bytes = t;
     return FDTD_OK;
 }
 

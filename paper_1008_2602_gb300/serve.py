@@ -43,16 +43,12 @@ class Result:
 
 
 def estimate_bytes(prob, precision: str = "fp32") -> int:
-    """Device bytes of a board: two parities of six fields, ids, UPML
-    auxiliaries (bounded by six per UPML node), traces and spectra."""
-    es = 4 if precision == "fp32" else 2
-    pitch = ((prob.nx + 1 + 63) // 64) * 64
-    nodes = pitch * (prob.ny + 1) * (prob.nz + 1)
-    d = prob.upml_depth
-    inner = max(0, prob.nx - d[0] - d[1]) * max(0, prob.ny - d[2] - d[3]) * max(0, prob.nz - d[4] - d[5])
-    upml = max(0, (prob.nx + 1) * (prob.ny + 1) * (prob.nz + 1) - inner)
-    P = len(prob.probes)
-    return int(nodes * (12 * es + 2) + upml * 6 * 4 + P * prob.n_steps * 4 + P * 2048 * 16 + (1 << 20))
+    """Device bytes a board will hold, asked of the library before the board
+    exists (fdtd_device_bytes: the library's own layout of fields, ids, UPML
+    auxiliaries, traces and spectra; 16-bit ids assumed, so at most one byte
+    per node and 1 MB above what the board then reports)."""
+    from . import solver
+    return solver.device_bytes(prob, precision)
 
 
 class CudaBackend:

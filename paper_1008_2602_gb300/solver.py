@@ -26,16 +26,34 @@ def _stream_ptr(stream) -> Optional[int]:
     return int(stream.cuda_stream)   # a torch.cuda.Stream
 
 
+def problem_structs(prob):
+    """The fdtd_grid and fdtd_boundary of a workloads.Problem."""
+    g = C.fdtd_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.courant, prob.dt)
+    b = C.fdtd_boundary()
+    b.depth[:] = list(prob.upml_depth)
+    b.m, b.R0, b.kappa_max = prob.upml_m, prob.upml_R0, prob.upml_kappa_max
+    b.wall[:] = list(prob.walls)
+    return g, b
+
+
+def device_bytes(prob, precision: str = "fp32") -> int:
+    """Device memory the board needs (fdtd_device_bytes, asked of the library
+    on the host, without a device)."""
+    g, b = problem_structs(prob)
+    n_src = len(np.asarray(prob.sources).reshape(-1, 4)) + len(np.asarray(prob.vsources).reshape(-1, 4))
+    n_prb = len(np.asarray(prob.probes).reshape(-1, 4))
+    out = ctypes.c_longlong()
+    C.fdtd_device_bytes(ctypes.byref(g), ctypes.byref(b), PRECISION[precision], n_src, n_prb,
+                        int(prob.n_steps) if n_prb else 0, float(prob.f_max) if prob.f_max else -1.0, ctypes.byref(out))
+    return int(out.value)
+
+
 class Solver:
     def __init__(self, prob, precision: str = "fp32", stream=None, tuning: Optional[dict] = None,
                  spectrum: bool = True):
         self.problem = prob
         self.precision = precision
-        g = C.fdtd_grid(prob.nx, prob.ny, prob.nz, prob.dx, prob.dy, prob.dz, prob.courant, prob.dt)
-        b = C.fdtd_boundary()
-        b.depth[:] = list(prob.upml_depth)
-        b.m, b.R0, b.kappa_max = prob.upml_m, prob.upml_R0, prob.upml_kappa_max
-        b.wall[:] = list(prob.walls)
+        g, b = problem_structs(prob)
         self._mat = np.ascontiguousarray(prob.mat, dtype=np.uint8)
         self._eps = np.ascontiguousarray(prob.eps_r, dtype=np.float64)
         boxes = np.ascontiguousarray(prob.pec_boxes, dtype=np.int32).reshape(-1, 6)

@@ -460,3 +460,21 @@ def test_no_sources_no_probes(fdtd):
     for c in range(6):
         assert not np.any(s.field(c))
     s.close()
+
+
+@pytest.mark.parametrize("prob", ["small", "random", "multilayer_q"])
+def test_device_bytes_bounds_what_a_board_allocates(fdtd, prob):
+    """fdtd_device_bytes (host only, used for admission) against the device
+    memory the created board reports after its first step: never below it,
+    and above it by exactly the id width saving (one byte per node and the
+    table's 65536 - 256 rows) when the board's ids are 8-bit."""
+    p = {"small": W.small_pcb(), "random": W.random_problem(61, 33, 25, 19, upml=3, n_steps=40),
+         "multilayer_q": W.multilayer_board(scale=4, n_steps=50)}[prob]
+    est = fdtd.device_bytes(p)
+    s = fdtd.Solver(p)
+    s.step(1)
+    inf = s.info()
+    s.close()
+    nodes = ((p.nx + 1 + 63) // 64) * 64 * (p.ny + 1) * (p.nz + 1)
+    slack = 0 if inf["n_combo"] > 256 else nodes + (65536 - 256) * 16
+    assert est == inf["device_bytes"] + slack, (est, inf["device_bytes"], slack)

@@ -149,3 +149,22 @@ def test_router_balances_one_stream_across_ranks():
         work[k] += r.problem.cells * r.problem.n_steps
     assert max(work) <= 1.5 * (sum(work) / 4)
     assert serve.route(reqs, 1) == [0] * len(reqs)
+
+
+def test_device_bytes_follows_the_library_layout():
+    """fdtd_device_bytes (host only): a board without UPML or ports is its two
+    field parities, 16-bit ids, the 65536-row table, the UPML factor tables
+    and the fixed scratch, to the byte; UPML auxiliaries and probe traces add
+    to it, and FP16 storage halves the fields."""
+    from paper_1008_2602_gb300 import solver
+    p = W.box(20, 10, 6)
+    nodes = 64 * 11 * 7
+    base = solver.device_bytes(p)
+    fields = 12 * nodes * 4
+    assert base > fields + 2 * nodes + 65536 * 16
+    assert base < fields + 2 * nodes + 65536 * 16 + 64 * 1024
+    assert solver.device_bytes(p, "fp16") == base - 6 * nodes * 4
+    up = solver.device_bytes(p.replace(upml_depth=(3,) * 6))
+    assert up > base + 8 * 1000                 # UPML auxiliaries (two or more per graded node)
+    with_probes = solver.device_bytes(W.add_ports(p, [(5, 5, 3, 2)], [(6, 5, 3, 2)] * 3, n_steps=1000))
+    assert with_probes >= base + 3 * 1000 * 4
