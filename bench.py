@@ -227,6 +227,10 @@ def run_single(args, world, rank, local):
     t_zp = phase[1] / 1e3 / n_launch
     achieved = alg_bytes / t_int / 1e9
     zp_bytes = (bytes_per_node + 16) * upml_nodes
+    # the two slab launches together: each slab node's 12 field values + id
+    # (H and E halves), and every slab auxiliary read and written once
+    t_sl = (phase[0] + phase[3]) / 1e3 / n_launch
+    sl_bytes = bytes_per_node * inf["slab_nodes"] + 8 * inf["slab_aux_values"]
     # whole leapfrog step: every node's 12 field values + id, the z-UPML
     # auxiliaries and the slab auxiliaries (each read and written once)
     step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 16 * upml_nodes + 8 * inf["slab_aux_values"]
@@ -285,6 +289,12 @@ def run_single(args, world, rank, local):
                            "units_per_launch": upml_nodes, "mean_launch_ms": round(t_zp * 1e3, 5),
                            "achieved": round(zp_bytes / t_zp / 1e9, 1) if t_zp > 0 else None,
                            "frac": round(zp_bytes / t_zp / 1e9 / peak, 4) if t_zp > 0 else None},
+        "roofline_slab": {"kernel": "k_slab_h + k_slab_e (UPML faces, edges, corners, z-UPML rings, wall planes)",
+                          "bytes_per_unit": bytes_per_node, "aux_bytes_per_value": 8,
+                          "units_per_launch": int(inf["slab_nodes"]), "aux_values": int(inf["slab_aux_values"]),
+                          "mean_launch_ms": round(t_sl * 1e3, 5),
+                          "achieved": round(sl_bytes / t_sl / 1e9, 1) if t_sl > 0 else None,
+                          "frac": round(sl_bytes / t_sl / 1e9 / peak, 4) if t_sl > 0 else None},
         "tuning": {"tile_x": args.tile_x or "default", "tile_y": args.tile_y or "default",
                    "zseg": args.zseg or "default"},
         "gpu_launches": int(args.steps * (window * (5 if upml_nodes else 4) + 2)),
