@@ -219,15 +219,20 @@ bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, B
                   long long zplanes[2])
 {
     const int nx = g.nx, ny = g.ny, nz = g.nz;
-    // fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) and the slabs around it
+    // fused region F = [ix0,ix1) x [iy0,iy1) x [zlo,nz) and the slabs around it.
+    // Under a z-UPML the bottom wall is PEC: its plane k = 0 holds the H~x, H~y
+    // and E_z samples half a cell up (its tangential E is PEC, and H~z there
+    // sees only the curl of that zero E), so the z-UPML launch works it as
+    // its first plane (zlo = 0).  Otherwise k = 0 stays a slab plane.
     h.ix0 = std::max(bnd.depth[0], 1); h.ix1 = nx - bnd.depth[1];
     h.iy0 = std::max(bnd.depth[2], 1); h.iy1 = ny - bnd.depth[3];
     h.iz0 = std::max(bnd.depth[4], 1); h.iz1 = nz - bnd.depth[5];
+    h.zlo = bnd.depth[4] > 0 ? 0 : 1;
     std::vector<std::array<int, 6>> boxes;
     const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
     if (!fused) {
         h.ix0 = h.ix1 = h.iy0 = h.iy1 = 0;
-        h.iz0 = 1; h.iz1 = nz;
+        h.iz0 = 1; h.iz1 = nz; h.zlo = 1;
         boxes.push_back({0, nx + 1, 0, ny + 1, 0, nz + 1});
     } else {
         // The slabs are split where the set of graded axes changes, so that each
@@ -254,9 +259,10 @@ bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, B
             for (int yb = 0; yb < 3; yb += 2)
                 for (int xb = 0; xb < 3; ++xb) boxes.push_back({xs[xb], xs[xb + 1], ys[yb], ys[yb + 1], zs[zb], zs[zb + 1]});
             for (int xb = 0; xb < 3; xb += 2) boxes.push_back({xs[xb], xs[xb + 1], h.iy0, h.iy1, zs[zb], zs[zb + 1]});
-            // the wall plane of the interior columns (the fused kernels start at k = 1)
+            // the wall plane of the interior columns, unless the fused z-UPML
+            // launch works it (zlo = 0) or it is a PEC high plane
             const int kw = zb == 0 ? 0 : nz;
-            if (kw < ze) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
+            if (kw < ze && !(kw == 0 && h.zlo == 0)) boxes.push_back({h.ix0, h.ix1, h.iy0, h.iy1, kw, kw + 1});
         }
         // planes between the z-UPML layers: y faces, x faces, the four corner columns
         for (int yb = 0; yb < 3; yb += 2) boxes.push_back({h.ix0, h.ix1, ys[yb], ys[yb + 1], zs[1], zs[2]});
@@ -305,10 +311,10 @@ bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, B
         ++h.n_slab;
     }
     h.slab_blocks = blocks;
-    // z-UPML boxes of the fused region: lower planes [1, iz0), upper [iz1, nz)
+    // z-UPML boxes of the fused region: lower planes [zlo, iz0), upper [iz1, nz)
     h.zpitch = fused ? ((h.ix1 - h.ix0) + 7) & ~7 : 0;
     for (int bx = 0; bx < 2; ++bx) {
-        const long long planes = bx == 0 ? (long long)h.iz0 - 1 : (long long)nz - h.iz1;
+        const long long planes = bx == 0 ? (long long)h.iz0 - h.zlo : (long long)nz - h.iz1;
         zplanes[bx] = fused && planes > 0 ? planes : 0;
     }
     return true;
@@ -697,14 +703,14 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
 }
 
 // Fused-kernel items of a board: (x tile, y tile, z segment), x fastest.  The
-// interior launch covers planes [iz0, iz1), the z-UPML launch [1, iz0) and
+// interior launch covers planes [iz0, iz1), the z-UPML launch [zlo, iz0) and
 // [max(iz1, iz0), nz); the device decodes items the same way.
 long long fused_items(const Board &h, const fdtd_tuning &t, bool zp)
 {
     const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0;
     if (Lx <= 0 || Ly <= 0 || h.nz < 2) return 0;
     auto segs = [&](long long k0, long long k1) { return k1 > k0 ? (k1 - k0 + t.zseg - 1) / t.zseg : 0; };
-    const long long nseg = zp ? segs(1, h.iz0) + segs(std::max(h.iz1, h.iz0), h.nz) : segs(h.iz0, h.iz1);
+    const long long nseg = zp ? segs(h.zlo, h.iz0) + segs(std::max(h.iz1, h.iz0), h.nz) : segs(h.iz0, h.iz1);
     return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * nseg;
 }
 
@@ -1736,7 +1742,7 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     info->n_total_steps = h.n_total;
     info->n_bins = h.n_bins;
     info->precision = c->prec;
-    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - 1;
+    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = (long long)h.nz - h.zlo;
     info->interior_nodes = (Lx > 0 && Ly > 0 && Lz > 0) ? Lx * Ly * Lz : 0;
     info->fused_upml_nodes = info->interior_nodes > 0 ? Lx * Ly * (c->zplanes[0] + c->zplanes[1]) : 0;
     long long sn = 0, sa = 0;

@@ -30,13 +30,14 @@
 // (E - ce D~ is constant).  An auxiliary is kept only where the factors along
 // w are graded or both w+1 and w+2 are.
 //
-// Work split.  The fused region F = [ix0,ix1) x [iy0,iy1) x [1,nz) (the
-// columns outside the x/y UPML, minus the two outer z planes) is updated by
-// one fused H+E kernel that marches z; its z-UPML planes ([1,iz0) and
-// [iz1,nz)) have sigma_z only, so they carry D~y, D~z (updated in place) and
-// B~y, B~z (ping-ponged, since neighbouring tiles recompute halo H from them)
-// in compact [k][j][i] boxes.  Everything else (x/y UPML slabs with their
-// edges and corners, and the two outer z planes) is updated by generic slab
+// Work split.  The fused region F = [ix0,ix1) x [iy0,iy1) x [zlo,nz) (the
+// columns outside the x/y UPML, minus the outer z planes; zlo = 0 under a
+// z-UPML, whose PEC wall plane k = 0 the z-UPML launch works) is updated by
+// one fused H+E kernel that marches z; its z-UPML planes ([zlo,iz0) and
+// [iz1,nz)) have sigma_z only, so they carry D~z (updated in place) and B~z
+// (ping-ponged, since neighbouring tiles recompute halo H from it) in compact
+// [k][j][i] boxes.  Everything else (x/y UPML slabs with their
+// edges and corners, and the outer z planes) is updated by generic slab
 // kernels whose auxiliary D~/B~ live in compact [k][j][i] boxes per slab, only
 // for components whose recurrence there is not trivial.
 #pragma once
@@ -106,7 +107,8 @@ struct Board {
     int wall[6];
     int depth[6];                 // UPML cells per face
     int ix0, ix1, iy0, iy1, iz0, iz1;   // fused xy box; non-UPML z range [iz0, iz1)
-    // z-UPML boxes of the fused region: [0] k in [1, iz0), [1] k in [iz1, nz);
+    int zlo;                            // first plane of the fused region: 0 under a z-UPML (PEC wall), else 1
+    // z-UPML boxes of the fused region: [0] k in [zlo, iz0), [1] k in [iz1, nz);
     // element (i, j, k) at ((k - k0) * (iy1 - iy0) + j - iy0) * zpitch + i - ix0.
     // With sigma_z alone, B~x, B~y and D~x, D~y need no storage (see the
     // auxiliary rule below); B~z and D~z are kept.
@@ -153,7 +155,7 @@ struct Plan {
     int tile_x, tile_y, zseg;     // interior tile (threads in x, y) and z-segment
     Board *const *boards;         // [nb] device pointers
     const long long *int_prefix;  // [nb + 1] interior-kernel items (planes [iz0, iz1))
-    const long long *zp_prefix;   // [nb + 1] z-UPML-kernel items (planes [1, iz0) and [iz1, nz))
+    const long long *zp_prefix;   // [nb + 1] z-UPML-kernel items (planes [zlo, iz0) and [iz1, nz))
     const long long *slab_prefix; // [nb + 1] slab blocks
     const SlabBlock *slab_blk;    // [n_slab] per-block descriptors
     const long long *dft_prefix;  // [nb + 1] DFT warps

@@ -2,8 +2,8 @@
 //
 // One step (Model section: H at half steps from E, then E from H and J) is
 // five launches over a Plan (one board or a batch of boards):
-//   k_slab_h        H^{n+1/2} (and B~) on the x/y UPML slabs and the two
-//                   outer z planes                                  (Eqs. 1-5)
+//   k_slab_h        H^{n+1/2} (and B~) on the x/y UPML slabs and the outer
+//                   z planes                                        (Eqs. 1-5)
 //   k_fused<..,1>   fused H^{n+1/2} and E^{n+1} on the interior columns'
 //                   z-UPML planes (sigma_z only; B~z, D~z staged by TMA)
 //   k_fused<..,0>   fused H^{n+1/2} and E^{n+1} on the interior columns'
@@ -128,7 +128,7 @@ __device__ __forceinline__ int zbox_of(const Board *B, int k) { return k < B->iz
 
 __device__ __forceinline__ long long zaux_index(const Board *B, int box, int i, int j, int k)
 {
-    const int k0 = box == 1 ? 1 : B->iz1;
+    const int k0 = box == 1 ? B->zlo : B->iz1;
     return ((long long)(k - k0) * (B->iy1 - B->iy0) + (j - B->iy0)) * (long long)B->zpitch + (i - B->ix0);
 }
 
@@ -330,7 +330,7 @@ struct Tile {
 
 // Items of one board: x tiles fastest, then y tiles, then z segments.  The
 // interior kernel (ZP false) covers planes [iz0, iz1); the z-UPML kernel
-// covers [1, iz0) and [max(iz1, iz0), nz).  kstart is the plane below the
+// covers [zlo, iz0) and [max(iz1, iz0), nz).  kstart is the plane below the
 // segment when the tile recomputes its H~ there, else kb (that plane's H~ is
 // then read from the output: an outer plane, or a z-UPML plane written by the
 // z-UPML launch, which runs first).
@@ -360,15 +360,19 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
         t.ke = min(t.kb + zs, iz1);
         t.kstart = t.kb - 1 >= iz0 ? t.kb - 1 : t.kb;
     } else {
-        const int nlo = (iz0 - 1 + zs - 1) / zs;
+        // planes [zlo, iz0) and [max(iz1, iz0), nz); a segment starting at
+        // plane 0 (zlo = 0) has no plane below, one starting at plane 1
+        // (zlo = 1) reads the slab's wall plane below
+        const int zlo = t.B->zlo;
+        const int nlo = (iz0 - zlo + zs - 1) / zs;
         if (tz < nlo) {
-            t.kb = 1 + tz * zs;
+            t.kb = zlo + tz * zs;
             t.ke = min(t.kb + zs, iz0);
         } else {
             t.kb = max(iz1, iz0) + (tz - nlo) * zs;
             t.ke = min(t.kb + zs, t.B->nz);
         }
-        t.kstart = t.kb >= 2 ? t.kb - 1 : t.kb;
+        t.kstart = t.kb > zlo ? t.kb - 1 : t.kb;
     }
     return t;
 }
@@ -466,7 +470,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
                     tma_load_3d(st + St::C_OFF, tm + kTmCid, xc0, t.j0, p, &full[s]);
                 }
                 if (zb) {
-                    const int bx = zb - 1, kz = p - (zb == 1 ? 1 : B->iz1);
+                    const int bx = zb - 1, kz = p - (zb == 1 ? B->zlo : B->iz1);
                     unsigned char *a = st + St::A_OFF;
                     tma_load_3d(a, tm + tm_zb(bx, t.par), xa0, t.j0 - 1 - B->iy0, kz, &full[s]);
                     tma_load_3d(a + St::B_CS * 4, tm + tm_zd(bx), xa0, t.j0 - B->iy0, kz, &full[s]);
@@ -529,7 +533,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
         float2 hk1x[TYW], hk1y[TYW];   // H~x, H~y of the previous plane, per row
 #pragma unroll
         for (int r = 0; r < TYW; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
-        if (kstart == kb) {         // plane kb-1 is not recomputed: read its H~
+        if (kstart == kb && kb > 0) {   // plane kb-1 is not recomputed: read its H~ (none below plane 0)
 #pragma unroll
             for (int r = 0; r < TYW; ++r)
                 if (jb + r < iy1) {
@@ -558,7 +562,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
             if (ZP && zb) {
                 z.zi = B->cw[2][0][k];
                 z.zh = B->cw[2][1][k];
-                za = (long long)(k - (zb == 1 ? 1 : iz1)) * zplane + zcol;
+                za = (long long)(k - (zb == 1 ? B->zlo : iz1)) * zplane + zcol;
                 nzbz = B->zB[zb - 1][par ^ 1];
                 zdz = B->zD[zb - 1];
             }
