@@ -255,8 +255,7 @@ def run_single(args, world, rank, local):
         te1 = time.perf_counter()
         et = te1 - te0
         et = _max_over_ranks(et)
-        pitch = ((prob.nx + 1 + 63) // 64) * 64
-        h2d = pitch * (prob.ny + 1) * (prob.nz + 1) + 256 * 16
+        h2d = inf["pitch"] * (prob.ny + 1) * (prob.nz + 1) + 256 * 16   # 8-bit ids and their table
         e2e = {"value": float(cells) * window * args.e2e_steps * world / et / 1e9, "unit": "Gcell-updates/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(spec.nbytes),
                "steps": args.e2e_steps,

@@ -99,6 +99,7 @@ typedef struct {
     long long device_bytes;    /* device memory held */
     int n_combo;               /* distinct per-node E-coefficient triples */
     long long slab_aux_values; /* auxiliary D~/B~ values held by the slabs (read and written once per step) */
+    int pitch;                 /* row pitch of the device field and id arrays, elements (nx + 1 rounded up) */
 } fdtd_info_t;
 
 /* Create a board (Model section, Fig. 1).

@@ -41,7 +41,8 @@ class fdtd_info_t(ctypes.Structure):
                 ("n_sources", c_int), ("n_probes", c_int), ("n_total_steps", c_int), ("n_bins", c_int),
                 ("precision", c_int), ("interior_nodes", c_longlong), ("fused_upml_nodes", c_longlong),
                 ("slab_nodes", c_longlong),
-                ("device_bytes", c_longlong), ("n_combo", c_int), ("slab_aux_values", c_longlong)]
+                ("device_bytes", c_longlong), ("n_combo", c_int), ("slab_aux_values", c_longlong),
+                ("pitch", c_int)]
 
 
 class fdtd_tuning(ctypes.Structure):

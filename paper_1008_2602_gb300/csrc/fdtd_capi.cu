@@ -228,6 +228,18 @@ bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, B
     h.iy0 = std::max(bnd.depth[2], 1); h.iy1 = ny - bnd.depth[3];
     h.iz0 = std::max(bnd.depth[4], 1); h.iz1 = nz - bnd.depth[5];
     h.zlo = bnd.depth[4] > 0 ? 0 : 1;
+    // The fused region's x bounds are rounded inward to whole 32-byte sectors
+    // of a field row (8 FP32 or 16 FP16 nodes); the extra columns are plain
+    // nodes that the slab kernels update.  Then no sector is written partly by
+    // a slab launch and partly by a fused launch, which would leave it
+    // partially written in L2 between the two launches.  A slab row costs
+    // about the same at 12 and at 16 nodes (its price is the number of separate
+    // row segments a warp touches, not their length).
+    {
+        const int xa = h.prec == kFP16 ? 16 : 8;
+        const int ax0 = (h.ix0 + xa - 1) / xa * xa, ax1 = h.ix1 / xa * xa;
+        if (ax1 - ax0 >= xa) { h.ix0 = ax0; h.ix1 = ax1; }
+    }
     std::vector<std::array<int, 6>> boxes;
     const bool fused = h.ix1 > h.ix0 && h.iy1 > h.iy0 && nz >= 2;
     if (!fused) {
@@ -993,7 +1005,7 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
 
     Board &h = c->h;
     h.nx = grid->nx; h.ny = grid->ny; h.nz = grid->nz;
-    h.pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    h.pitch = row_pitch(grid->nx);
     h.plane = (long long)h.pitch * (grid->ny + 1);
     h.nodes = h.plane * (grid->nz + 1);
     if (h.nodes >= (1LL << 31)) { fdtd_destroy(c); return fail(FDTD_EINVAL, "grid too large (>= 2^31 nodes)"); }
@@ -1649,7 +1661,7 @@ int fdtd_node_coefficients(const fdtd_grid *grid, const uint8_t *mat_ids, const 
     c.eps.assign(eps_r, eps_r + n_mat);
     if (n_pec > 0) c.boxes.assign(pec, pec + n_pec);
     if (pec_mask) c.mask.assign(pec_mask, pec_mask + (size_t)grid->nx * grid->ny * grid->nz);
-    c.h.pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    c.h.pitch = row_pitch(grid->nx);
     const int NX = grid->nx + 1, NY = grid->ny + 1, NZ = grid->nz + 1;
     IdScratch &scratch = id_scratch();
     std::lock_guard<std::mutex> hold(scratch.lock);
@@ -1692,7 +1704,7 @@ int fdtd_device_bytes(const fdtd_grid *grid, const fdtd_boundary *bnd, int preci
     const uint8_t mat0 = 0;
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return fail(FDTD_EINVAL, "grid must have at least one cell per axis");
     if (int r = check_problem(grid, &mat0, &one, 1, nullptr, 0, bnd)) return r;
-    const long long pitch = ((grid->nx + 1 + kPitchAlign - 1) / kPitchAlign) * kPitchAlign;
+    const long long pitch = row_pitch(grid->nx);
     const long long nodes = pitch * (grid->ny + 1) * (grid->nz + 1);
     const double dt = grid_dt(*grid);
     Axes A;
@@ -1700,6 +1712,7 @@ int fdtd_device_bytes(const fdtd_grid *grid, const fdtd_boundary *bnd, int preci
     std::unique_ptr<Board> hb(new Board());
     Board &h = *hb;
     h.nx = grid->nx; h.ny = grid->ny; h.nz = grid->nz;
+    h.prec = precision;
     bool aux[kMaxSlab][6];
     long long zplanes[2] = {0, 0};
     if (!layout_board(*grid, *bnd, A, h, aux, zplanes)) return fail(FDTD_EINVAL, "internal: too many slab boxes");
@@ -1753,6 +1766,7 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     }
     info->slab_nodes = sn;
     info->slab_aux_values = sa;
+    info->pitch = h.pitch;
     info->device_bytes = c->device_bytes;
     info->n_combo = c->n_combo;
     return FDTD_OK;

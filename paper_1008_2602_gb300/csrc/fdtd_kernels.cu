@@ -841,15 +841,23 @@ struct Word<__half> {
 };
 
 // Coefficient id of node idx from the word holding it (8- or 16-bit ids).
-__device__ __forceinline__ const void *cid_word(const Board *B, long long idx)
+__device__ __forceinline__ const void *cid_word(const void *cid, int id16, long long idx)
 {
-    return B->id16 ? (const void *)((uintptr_t)((const uint16_t *)B->cid + idx) & ~(uintptr_t)3)
-                   : (const void *)((uintptr_t)((const uint8_t *)B->cid + idx) & ~(uintptr_t)3);
+    return id16 ? (const void *)((uintptr_t)((const uint16_t *)cid + idx) & ~(uintptr_t)3)
+                : (const void *)((uintptr_t)((const uint8_t *)cid + idx) & ~(uintptr_t)3);
 }
-__device__ __forceinline__ int cid_get(const Board *B, float w, long long idx)
+__device__ __forceinline__ int cid_get(int id16, float w, long long idx)
 {
     const unsigned b = __float_as_uint(w);
-    return B->id16 ? (int)((idx & 1) ? b >> 16 : b & 0xffffu) : (int)((b >> (8 * (int)(idx & 3))) & 0xffu);
+    return id16 ? (int)((idx & 1) ? b >> 16 : b & 0xffffu) : (int)((b >> (8 * (int)(idx & 3))) & 0xffu);
+}
+
+// One row of a 1D UPML factor table through the read-only cache (the
+// tables are 16-byte aligned, one Coef per position).
+__device__ __forceinline__ Coef ldcoef(const Coef *p)
+{
+    const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+    return Coef{v.x, v.y, v.z, v.w};
 }
 
 // Ring slots per thread (nodes in flight + 1), words per node and resident
@@ -1012,13 +1020,19 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
         const bool ym = sc.ym;
         const long long idx0 = (long long)k0 * P + (long long)j0 * X + i;
         const long long didx = ym ? X : P;
+        const Coef *const cy0 = B->cw[1][0], *const cy1 = B->cw[1][1];
+        const Coef *const cz0 = B->cw[2][0], *const cz1 = B->cw[2][1];
+        Coef y0 = ldcoef(cy0 + j0), y1 = ldcoef(cy1 + j0), z0 = ldcoef(cz0 + k0), z1 = ldcoef(cz1 + k0);
+        const void *const cid = B->cid;
+        const int id16 = B->id16;
+        const float4 *const ctab = B->ctab;
         auto issue = [&](int m) {
             if (m < cnt) {
                 const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
                 const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
                 const int oy1 = j == ny ? -X : 0, oy0 = j == 0 ? 0 : -X;
                 const long long oz1 = k == nz ? -P : 0, oz0 = k == 0 ? 0 : -P;
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eID), cid_word(B, idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eID), cid_word(cid, id16, idx));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY1), Word<T>::at(F.ohz + idx + oy1));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY0), Word<T>::at(F.ohz + idx + oy0));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYZ1), Word<T>::at(F.ohy + idx + oz1));
@@ -1057,8 +1071,11 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
             auto w = [&](int word) { return *ring_at<kSlabEStages, kSlabEWords>(my, m, word); };
             const bool yhi = j == ny, ylo = j == 0, zhi = k == nz, zlo = k == 0;
             const float syh = hsign(yhi, w3), syl = hsign(ylo, w2), szh = hsign(zhi, w5), szl = hsign(zlo, w4);
-            const float4 ce = __ldg(B->ctab + cid_get(B, w(eID), idx));
-            const Coef y0 = B->cw[1][0][j], y1 = B->cw[1][1][j], z0 = B->cw[2][0][k], z1 = B->cw[2][1][k];
+            const float4 ce = __ldg(ctab + cid_get(id16, w(eID), idx));
+            if (m > 0) {
+                if (ym) { y0 = ldcoef(cy0 + j); y1 = ldcoef(cy1 + j); }
+                else { z0 = ldcoef(cz0 + k); z1 = ldcoef(cz1 + k); }
+            }
             if (ym || m == 0) {
                 hyz0 = Word<T>::get(w(eHYZ0), idx + oz0);
                 hxz0 = Word<T>::get(w(eHXZ0), idx + oz0);

@@ -475,6 +475,6 @@ def test_device_bytes_bounds_what_a_board_allocates(fdtd, prob):
     s.step(1)
     inf = s.info()
     s.close()
-    nodes = ((p.nx + 1 + 63) // 64) * 64 * (p.ny + 1) * (p.nz + 1)
+    nodes = inf["pitch"] * (p.ny + 1) * (p.nz + 1)
     slack = 0 if inf["n_combo"] > 256 else nodes + (65536 - 256) * 16
     assert est == inf["device_bytes"] + slack, (est, inf["device_bytes"], slack)

@@ -7,7 +7,11 @@ against the FP64 oracle:
   FP16 <= 1e-2 (the target for reduced storage);
 * FP32 and FP16: the spectral peak of every probe with signal stays within
   one running-DFT bin of the oracle's (1000 steps give coarse bins, where a
-  broad peak can sit between two nearly equal bins).
+  broad peak can sit between two nearly equal bins), or lands on a bin whose
+  oracle magnitude ties the oracle's peak within the mode's spectral error
+  (several probes of this board have two separate peaks within 1 % of each
+  other, e.g. probe 51: bins 1 and 8 at a ratio of 0.996, which FP16
+  rounding may order either way).
 """
 import numpy as np
 import pytest
@@ -18,6 +22,7 @@ from paper_1008_2602_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-4, "fp16": 1e-2}
+PEAK_TIE = {"fp32": 1e-3, "fp16": 2e-2}   # relative magnitude within which two peaks tie
 
 
 @pytest.fixture(scope="module")
@@ -60,5 +65,7 @@ def test_storage_mode_error(runs, prec):
     assert e_oracle <= TOL[prec], (prec, e_oracle, e_fp32)
     assert e_fp32 <= TOL[prec] + 1e-4
     for q in np.nonzero(live)[0]:
-        shift = np.argmax(np.abs(got["spectra"][q][1:])) - np.argmax(np.abs(ref["spectra"][q][1:]))
-        assert abs(int(shift)) <= 1, (q, shift)
+        g = np.abs(got["spectra"][q][1:])
+        r = np.abs(ref["spectra"][q][1:])
+        i, j = int(np.argmax(g)), int(np.argmax(r))
+        assert abs(i - j) <= 1 or r[i] >= (1 - PEAK_TIE[prec]) * r[j], (q, i, j, float(r[i] / r[j]))

@@ -158,7 +158,7 @@ def test_device_bytes_follows_the_library_layout():
     to it, and FP16 storage halves the fields."""
     from paper_1008_2602_gb300 import solver
     p = W.box(20, 10, 6)
-    nodes = 64 * 11 * 7
+    nodes = 32 * 11 * 7                 # rows of 21 nodes padded to a pitch of 32 (an odd multiple of 32)
     base = solver.device_bytes(p)
     fields = 12 * nodes * 4
     assert base > fields + 2 * nodes + 65536 * 16
