@@ -171,6 +171,7 @@ struct Plan {
     const long long *dft_prefix;  // [nb + 1] DFT warps
     long long n_int, n_zp, n_slab, n_dft;
     int *work;                    // fused-kernel work counters [interior, z-UPML] (zeroed before every launch)
+    int slots;                    // resident blocks of the fused launch (set by its launcher; orders the items)
 };
 
 // TMA descriptor slots of a board (3D maps: x, y, plane).

@@ -328,8 +328,17 @@ struct Tile {
     int i0, j0, kb, ke, kstart, par;
 };
 
-// Items of one board: x tiles fastest, then y tiles, then z segments.  The
-// interior kernel (ZP false) covers planes [iz0, iz1); the z-UPML kernel
+// Items of one board: x tiles fastest, then y tiles within a band of rows,
+// then z segments, then bands.  In the interior launch a band holds about as
+// many tiles as the launch has resident blocks, so the next z segment of a
+// tile starts about when the previous one ends, and the planes the two
+// segments both stage (the segment's E-only plane above, the next one's
+// recomputed plane below) are read while still in L2 (measured: interior
+// launch 0.384 -> 0.374 ms on the 880x680x100 board, 2 bands of 41 tile rows;
+// bands of 1.5, 0.5 or 0.25 waves were slower).  The z-UPML launch, whose layers split
+// into a long and a short segment, keeps one band (x, then y, then z; banding
+// it cost 2 %).  The interior kernel (ZP false) covers planes
+// [iz0, iz1); the z-UPML kernel
 // covers [zlo, iz0) and [max(iz1, iz0), nz).  kstart is the plane below the
 // segment when the tile recomputes its H~ there, else kb (that plane's H~ is
 // then read from the output: an outer plane, or a z-UPML plane written by the
@@ -349,12 +358,23 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
     const long long local = item - __ldg(prefix + b);
     constexpr int TX = kWarpCols * W;
     const int ntx = (t.B->ix1 - t.B->ix0 + TX - 1) / TX, nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
-    const int tx = (int)(local % ntx);
-    const long long rest = local / ntx;
-    const int ty = (int)(rest % nty), tz = (int)(rest / nty);
+    const int zs = plan.zseg, iz0 = t.B->iz0, iz1 = t.B->iz1;
+    int nseg;
+    if (!ZP) nseg = (iz1 - iz0 + zs - 1) / zs;
+    else nseg = (iz0 - t.B->zlo + zs - 1) / zs + (t.B->nz - max(iz1, iz0) + zs - 1) / zs;
+    // bands of about one wave of tiles, of equal height
+    const int wave_rows = max(1, plan.slots / ntx), nband = (nty + wave_rows - 1) / wave_rows;
+    const int band = ZP ? nty : (nty + nband - 1) / nband;
+    const long long per_band = (long long)ntx * band * nseg;
+    const int bi = (int)(local / per_band);
+    const long long within = local - bi * per_band;
+    const int rows = min(band, nty - bi * band);
+    const long long layer = (long long)ntx * rows;
+    const int tz = (int)(within / layer);
+    const int rem = (int)(within - tz * layer);
+    const int ty = bi * band + rem / ntx, tx = rem % ntx;
     t.i0 = t.B->ix0 + tx * TX;
     t.j0 = t.B->iy0 + ty * TY;
-    const int zs = plan.zseg, iz0 = t.B->iz0, iz1 = t.B->iz1;
     if (!ZP) {
         t.kb = iz0 + tz * zs;
         t.ke = min(t.kb + zs, iz1);
@@ -864,7 +884,7 @@ __device__ __forceinline__ Coef ldcoef(const Coef *p)
 // blocks per SM of the two slab kernels; the rings are sized so that the
 // blocks' shared memory fits an SM.
 constexpr int kSlabHStages = 4, kSlabHWords = 15, kSlabHBlocks = 3;
-constexpr int kSlabEStages = 4, kSlabEWords = 19, kSlabEBlocks = 2;
+constexpr int kSlabEStages = 4, kSlabEWords = 16, kSlabEBlocks = 2;
 constexpr int kSlabHSmem = kSlabHStages * kSlabHWords * kSlabThreads * 4;
 constexpr int kSlabESmem = kSlabEStages * kSlabEWords * kSlabThreads * 4;
 static_assert(kSlabHBlocks * (kSlabHSmem + 1024) <= 232448 && kSlabEBlocks * (kSlabESmem + 1024) <= 232448,
@@ -986,10 +1006,11 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabHBlocks) k_slab_h(Plan plan
 // `outside` the grid (PMC: odd mirror, -1; PEC: 0).
 __device__ __forceinline__ float hsign(bool outside, int wall) { return outside ? (wall == 1 ? -1.0f : 0.0f) : 1.0f; }
 
-enum SlabEWord {
-    eHZY1, eHZY0, eHYZ1, eHYZ0, eHXZ1, eHXZ0, eHZX1, eHZX0, eHYX1, eHYX0, eHXY1, eHXY0,
-    eEX, eEY, eEZ, eDX, eDY, eDZ, eID
-};
+// Ring words of a slab E node: H~ at the node and at its -x, -y, -z
+// neighbours (each loaded once; a neighbour across the low wall is clamped to
+// the node itself, and the image of H~ across a high wall is the -x/-y/-z
+// neighbour's value, picked after the load), E^n, the D~ auxiliaries, the id.
+enum SlabEWord { eHZ, eHZJ, eHZI, eHY, eHYI, eHYK, eHX, eHXJ, eHXK, eEX, eEY, eEZ, eDX, eDY, eDZ, eID };
 
 template <typename T>
 __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan)
@@ -1013,7 +1034,7 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
         // images across the x walls (fixed along the column)
         const bool xhi = i == nx, xlo = i == 0;
         const float sxh = hsign(xhi, wl[1]), sxl = hsign(xlo, wl[0]);
-        const int ox1 = xhi ? -1 : 0, ox0 = xlo ? 0 : -1;   // offsets of H at i and i-1 (or images)
+        const int ox0 = xlo ? 0 : -1;   // offset of H at i-1 (clamped at the low wall)
         // x factors fixed along the column: E_x (x half), E_y, E_z (x integer)
         const Coef x1 = B->cw[0][1][i], x0 = B->cw[0][0][i];
         const int j0 = sc.j, k0 = sc.k, cnt = sc.count;
@@ -1030,23 +1051,20 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
             if (m < cnt) {
                 const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
                 const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
-                const int oy1 = j == ny ? -X : 0, oy0 = j == 0 ? 0 : -X;
-                const long long oz1 = k == nz ? -P : 0, oz0 = k == 0 ? 0 : -P;
+                const int oy0 = j == 0 ? 0 : -X;
+                const long long oz0 = k == 0 ? 0 : -P;
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eID), cid_word(cid, id16, idx));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY1), Word<T>::at(F.ohz + idx + oy1));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZY0), Word<T>::at(F.ohz + idx + oy0));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYZ1), Word<T>::at(F.ohy + idx + oz1));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXZ1), Word<T>::at(F.ohx + idx + oz1));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZ), Word<T>::at(F.ohz + idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZJ), Word<T>::at(F.ohz + idx + oy0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZI), Word<T>::at(F.ohz + idx + ox0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHY), Word<T>::at(F.ohy + idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYI), Word<T>::at(F.ohy + idx + ox0));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHX), Word<T>::at(F.ohx + idx));
+                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXJ), Word<T>::at(F.ohx + idx + oy0));
                 if (ym || m == 0) {   // marching z, H~y and H~x at -z are the previous node's values
-                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYZ0), Word<T>::at(F.ohy + idx + oz0));
-                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXZ0), Word<T>::at(F.ohx + idx + oz0));
+                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYK), Word<T>::at(F.ohy + idx + oz0));
+                    cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXK), Word<T>::at(F.ohx + idx + oz0));
                 }
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZX1), Word<T>::at(F.ohz + idx + ox1));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHZX0), Word<T>::at(F.ohz + idx + ox0));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYX1), Word<T>::at(F.ohy + idx + ox1));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHYX0), Word<T>::at(F.ohy + idx + ox0));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXY1), Word<T>::at(F.ohx + idx + oy1));
-                cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eHXY0), Word<T>::at(F.ohx + idx + oy0));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEX), Word<T>::at(F.ex + idx));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEY), Word<T>::at(F.ey + idx));
                 cp_word(ring_at<kSlabEStages, kSlabEWords>(my, m, eEZ), Word<T>::at(F.ez + idx));
@@ -1058,7 +1076,7 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
         };
 #pragma unroll
         for (int m = 0; m < kSlabEStages - 1; ++m) issue(m);
-        float hyz0 = 0.f, hxz0 = 0.f;   // raw H~y, H~x at -z (carried along z)
+        float hyk = 0.f, hxk = 0.f;   // H~y, H~x at -z (carried along z)
 #pragma unroll
         for (int m = 0; m < kSlabKz; ++m) {
             if (m >= cnt) break;
@@ -1066,8 +1084,8 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
             cp_wait<kSlabEStages - 1>();
             const long long idx = idx0 + m * didx, t = sc.t + (long long)m * sc.tstep;
             const int j = ym ? j0 + m : j0, k = ym ? k0 : k0 + m;
-            const int oy1 = j == ny ? -X : 0, oy0 = j == 0 ? 0 : -X;
-            const long long oz1 = k == nz ? -P : 0, oz0 = k == 0 ? 0 : -P;
+            const int oy0 = j == 0 ? 0 : -X;
+            const long long oz0 = k == 0 ? 0 : -P;
             auto w = [&](int word) { return *ring_at<kSlabEStages, kSlabEWords>(my, m, word); };
             const bool yhi = j == ny, ylo = j == 0, zhi = k == nz, zlo = k == 0;
             const float syh = hsign(yhi, w3), syl = hsign(ylo, w2), szh = hsign(zhi, w5), szl = hsign(zlo, w4);
@@ -1077,40 +1095,40 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabEBlocks) k_slab_e(Plan plan
                 else { z0 = ldcoef(cz0 + k); z1 = ldcoef(cz1 + k); }
             }
             if (ym || m == 0) {
-                hyz0 = Word<T>::get(w(eHYZ0), idx + oz0);
-                hxz0 = Word<T>::get(w(eHXZ0), idx + oz0);
+                hyk = Word<T>::get(w(eHYK), idx + oz0);
+                hxk = Word<T>::get(w(eHXK), idx + oz0);
             }
-            const float hyz1 = Word<T>::get(w(eHYZ1), idx + oz1), hxz1 = Word<T>::get(w(eHXZ1), idx + oz1);
+            const float hz = Word<T>::get(w(eHZ), idx), hzj = Word<T>::get(w(eHZJ), idx + oy0);
+            const float hzi = Word<T>::get(w(eHZI), idx + ox0);
+            const float hy = Word<T>::get(w(eHY), idx), hyi = Word<T>::get(w(eHYI), idx + ox0);
+            const float hx = Word<T>::get(w(eHX), idx), hxj = Word<T>::get(w(eHXJ), idx + oy0);
             float dn;
             if (i < nx) {   // E_x(i+1/2, j, k)
                 const float e = upml_e2(Word<T>::get(w(eEX), idx),
-                                        curl2(syh * Word<T>::get(w(eHZY1), idx + oy1),
-                                              syl * Word<T>::get(w(eHZY0), idx + oy0), szh * hyz1, szl * hyz0, Sy,
-                                              Sz),
+                                        curl2(syh * (yhi ? hzj : hz), syl * hzj, szh * (zhi ? hyk : hy), szl * hyk,
+                                              Sy, Sz),
                                         ce.x, y0, z0, x1, ax != nullptr, ax ? w(eDX) : 0.f, dn);
                 Io<T>::st(F.oex + idx, e);
                 if (ax) ax[t] = dn;
             }
             if (j < ny) {   // E_y(i, j+1/2, k)
                 const float e = upml_e2(Word<T>::get(w(eEY), idx),
-                                        curl2(szh * hxz1, szl * hxz0, sxh * Word<T>::get(w(eHZX1), idx + ox1),
-                                              sxl * Word<T>::get(w(eHZX0), idx + ox0), Sz, Sx),
+                                        curl2(szh * (zhi ? hxk : hx), szl * hxk, sxh * (xhi ? hzi : hz), sxl * hzi,
+                                              Sz, Sx),
                                         ce.y, z0, x0, y1, ay != nullptr, ay ? w(eDY) : 0.f, dn);
                 Io<T>::st(F.oey + idx, e);
                 if (ay) ay[t] = dn;
             }
             if (k < nz) {   // E_z(i, j, k+1/2)
                 const float e = upml_e2(Word<T>::get(w(eEZ), idx),
-                                        curl2(sxh * Word<T>::get(w(eHYX1), idx + ox1),
-                                              sxl * Word<T>::get(w(eHYX0), idx + ox0),
-                                              syh * Word<T>::get(w(eHXY1), idx + oy1),
-                                              syl * Word<T>::get(w(eHXY0), idx + oy0), Sx, Sy),
+                                        curl2(sxh * (xhi ? hyi : hy), sxl * hyi, syh * (yhi ? hxj : hx), syl * hxj,
+                                              Sx, Sy),
                                         ce.z, x0, y0, z1, az != nullptr, az ? w(eDZ) : 0.f, dn);
                 Io<T>::st(F.oez + idx, e);
                 if (az) az[t] = dn;
             }
-            hyz0 = hyz1;   // the next node (k + 1 <= nz) reads H at k, which this node read unclamped
-            hxz0 = hxz1;
+            hyk = hy;   // the next node (k + 1 <= nz) reads H at k
+            hxk = hx;
         }
         cp_wait<0>();
     }
@@ -1368,7 +1386,9 @@ struct FusedCfg {
         const long long n = ZP ? plan.n_zp : plan.n_int;
         if (n <= 0) return;
         const int g = (int)(n < grid() ? n : grid());
-        k_fused<T, TY, W, NS, ZP, R><<<g, block(), L::BYTES, st>>>(plan);
+        Plan p = plan;
+        p.slots = grid();
+        k_fused<T, TY, W, NS, ZP, R><<<g, block(), L::BYTES, st>>>(p);
     }
 };
 
