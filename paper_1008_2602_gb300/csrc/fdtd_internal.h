@@ -200,7 +200,7 @@ inline bool fused_maps_match(const Board &h, int tile_x, int tile_y)
     return h.tm != nullptr && h.tm_tx == tile_x && h.tm_ty == tile_y;
 }
 
-constexpr int kSlabThreads = 256;
+constexpr int kSlabThreads = 128;
 constexpr int kSlabKz = 8;          // planes per slab-kernel thread
 constexpr int kDftProbeGroup = 4;
 
