@@ -1143,19 +1143,38 @@ __global__ void k_post(Plan plan)
     const int b = blockIdx.x;
     if (b >= plan.nb) return;
     Board *B = plan.boards[b];
-    if (!board_active(B)) return;
+    // What does not depend on the step is loaded before the step counter, so
+    // the descriptors, the field pointers and the counters arrive together
+    // (this kernel is a short chain of dependent loads between two launches).
+    const int tid = threadIdx.x;
+    const int n_src = B->n_src, n_probe = B->n_probe, n_total = B->n_total;
+    const bool par_src = B->src_distinct != 0;
+    const Source *const src = B->src;
+    const Probe *const probe = B->probe;
+    const double dt = B->dt;
+    const float scale = B->scale;
+    void *fp[2][3];
+#pragma unroll
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) fp[q][c] = B->f[q][c];
+    Source s0;
+    Probe q0;
+    if (tid < n_src) s0 = src[tid];
+    if (tid < n_probe) q0 = probe[tid];
     const long long step = *((volatile long long *)B->step);
+    if (step >= *((volatile long long *)B->stop)) return;
     const int out = (int)(step & 1) ^ 1;
+    auto field = [&](int par, int comp) -> T * { return (T *)(comp == 0 ? fp[par][0] : comp == 1 ? fp[par][1] : fp[par][2]); };
     // sources on distinct edges are independent: one thread each; sources
     // sharing an edge are applied in order by thread 0
-    const bool par_src = B->src_distinct != 0;
-    if (par_src || threadIdx.x == 0) {
-        const double t = ((double)step + 0.5) * B->dt;
-        for (int s = par_src ? (int)threadIdx.x : 0; s < B->n_src; s += par_src ? (int)blockDim.x : 1) {
-            const Source &S = B->src[s];
+    if (par_src || tid == 0) {
+        const double t = ((double)step + 0.5) * dt;
+        for (int s = par_src ? tid : 0; s < n_src; s += par_src ? (int)blockDim.x : 1) {
+            const Source S = (par_src && s == tid) ? s0 : src[s];
             const double u = (t - S.t0) / S.tau;
             const double w = S.J0 * u * exp(-u * u);   // Eq. 8 pulse: J, or Vs for a voltage source
-            T *e = (T *)B->f[out][S.comp] + S.node;
+            T *e = field(out, S.comp) + S.node;
             if (S.kind == kSrcCurrent) {
                 Io<T>::st(e, __fsub_rn(Io<T>::ldw(e), (float)(S.coef * w)));
             } else {
@@ -1163,21 +1182,21 @@ __global__ void k_post(Plan plan)
                 // in Ampere's law turns the plain update E_p = E^n + ce S curl into
                 // E^{n+1} = (E_p - beta E^n - gam Vs) / (1 + beta)
                 const double ep = Io<T>::ldw(e);
-                const double en = Io<T>::ldw((const T *)B->f[out ^ 1][S.comp] + S.node);
+                const double en = Io<T>::ldw((const T *)field(out ^ 1, S.comp) + S.node);
                 Io<T>::st(e, (float)((ep - S.beta * en - S.gam * w) / (1.0 + S.beta)));
             }
         }
     }
     __syncthreads();
-    const bool rec = step < (long long)B->n_total;
-    for (int p = threadIdx.x; p < B->n_probe; p += blockDim.x) {
-        const Probe &Q = B->probe[p];
-        const float v = Io<T>::ldw((const T *)B->f[out][Q.comp] + Q.node) * B->scale;
-        if (rec) B->trace[(long long)p * B->n_total + step] = v;
+    const bool rec = step < (long long)n_total;
+    for (int p = tid; p < n_probe; p += blockDim.x) {
+        const Probe Q = p == tid ? q0 : probe[p];
+        const float v = Io<T>::ldw((const T *)field(out, Q.comp) + Q.node) * scale;
+        if (rec) B->trace[(long long)p * n_total + step] = v;
         if (!isfinite(v)) atomicOr(B->status, 1);
     }
     __syncthreads();
-    if (threadIdx.x == 0) *((volatile long long *)B->step) = step + 1;
+    if (tid == 0) *((volatile long long *)B->step) = step + 1;
 }
 
 // ------------------------------------------------------------------ running DFT
