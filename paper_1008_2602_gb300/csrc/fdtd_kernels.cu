@@ -926,6 +926,10 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabHBlocks) k_slab_h(Plan plan
         const bool ym = sc.ym;
         const long long idx0 = (long long)k0 * P + (long long)j0 * X + i;
         const long long didx = ym ? X : P;
+        // y and z factors: only the marching axis' change from node to node
+        const Coef *const cy0 = B->cw[1][0], *const cy1 = B->cw[1][1];
+        const Coef *const cz0 = B->cw[2][0], *const cz1 = B->cw[2][1];
+        Coef y0 = ldcoef(cy0 + j0), y1 = ldcoef(cy1 + j0), z0 = ldcoef(cz0 + k0), z1 = ldcoef(cz1 + k0);
         // issue the loads of node m (empty group past the column's end)
         auto issue = [&](int m) {
             if (m < cnt) {
@@ -977,7 +981,10 @@ __global__ void __launch_bounds__(kSlabThreads, kSlabHBlocks) k_slab_h(Plan plan
             const float hxo = Word<T>::get(w(hHX), idx), hyo = Word<T>::get(w(hHY), idx);
             const float hzo = Word<T>::get(w(hHZ), idx);
             const bool yin = j < ny, zin = k < nz;
-            const Coef y1 = B->cw[1][1][j], y0 = B->cw[1][0][j], z1 = B->cw[2][1][k], z0 = B->cw[2][0][k];
+            if (m > 0) {
+                if (ym) { y0 = ldcoef(cy0 + j); y1 = ldcoef(cy1 + j); }
+                else { z0 = ldcoef(cz0 + k); z1 = ldcoef(cz1 + k); }
+            }
             float bn;
             if (yin && zin) {   // H_x(i, j+1/2, k+1/2)
                 const float h = upml_h2(hxo, curl2(ezj, ezc, eyu, eyc, Sy, Sz), y1, z1, x0, ax != nullptr,
