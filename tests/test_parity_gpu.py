@@ -219,6 +219,19 @@ def test_spectra_equal_fft_of_trace(fdtd):
     s.close()
 
 
+def test_row_bands_cover_every_tile(fdtd, ncpu):
+    """The interior launch takes its items in bands of tile rows of about one
+    wave of resident blocks.  A board one tile column wide and 624 tile rows
+    tall (more than one wave of 62x8 tiles) is worked in two bands; every
+    field element after 30 steps against the oracle."""
+    p = W.random_problem(41, 70, 5000, 14, upml=4, n_steps=30)
+    ref = oracle.run(p, n_threads=ncpu, fields=True)
+    s = fdtd.Solver(p, tuning=dict(tile_x=62, tile_y=8, zseg=10, graph_chunk=16))
+    s.run()
+    _fields_close(s, ref["fields"])
+    s.close()
+
+
 def test_chunking_and_tiling_do_not_change_results(fdtd):
     """Bitwise identical fields for different graph chunks, tile shapes and
     z-segments (halo recomputation equals the owner's value)."""
