@@ -185,8 +185,9 @@ def run_single(args, world, rank, local):
     prob = _workload(args.workload, seed_offset=rank)
     window = args.window
     s = solver.Solver(prob, precision=args.precision)
-    if args.tile_x or args.tile_y or args.zseg:
-        s.set_tuning(tile_x=args.tile_x, tile_y=args.tile_y, zseg=args.zseg)
+    if args.tile_x or args.tile_y or args.zseg or args.depth or args.pair_zseg:
+        s.set_tuning(tile_x=args.tile_x, tile_y=args.tile_y, zseg=args.zseg, depth=args.depth,
+                     pair_zseg=args.pair_zseg)
     inf = s.info()
     cells = prob.cells
     interior_nodes = inf["interior_nodes"]
@@ -223,7 +224,12 @@ def run_single(args, world, rank, local):
     int_nodes = interior_nodes - upml_nodes
     alg_bytes = bytes_per_node * int_nodes
     n_launch = window * args.steps
-    t_int = phase[2] / 1e3 / n_launch
+    depth = inf["depth"]
+    # depth 2: a window of `window` steps from an even step runs (window - 1) // 2
+    # two-step passes and one or two single steps (fdtd_step's split)
+    pairs = (window - 1) // 2 if depth == 2 and window >= 3 else 0
+    singles = window - 2 * pairs
+    t_int = phase[2] / 1e3 / (n_launch if depth == 1 else pairs * args.steps)
     t_zp = phase[1] / 1e3 / n_launch
     achieved = alg_bytes / t_int / 1e9
     zp_bytes = (bytes_per_node + 16) * upml_nodes
@@ -273,7 +279,9 @@ def run_single(args, world, rank, local):
         "phase_ms_per_leapfrog_step": {k: round(v / n_launch, 5) for k, v in
                                        zip(["slab_h", "fused_zupml", "fused_interior", "slab_e", "post", "dft_total"],
                                            phase)},
-        "roofline": {"bound": "hbm", "kernel": "k_fused interior launch (fused H+E, planes outside the z-UPML)",
+        "roofline": {"bound": "hbm", "kernel": "k_fused interior launch (fused H+E, planes outside the z-UPML)"
+                     if depth == 1 else "k_pair two-step interior pass (two leapfrog steps per launch; the phase "
+                     "also holds the window's single-step interior launches)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": traffic, "peak_source": peak_kind,
                      "bytes_per_unit": bytes_per_node, "units_per_launch": int_nodes,
@@ -295,8 +303,8 @@ def run_single(args, world, rank, local):
                           "achieved": round(sl_bytes / t_sl / 1e9, 1) if t_sl > 0 else None,
                           "frac": round(sl_bytes / t_sl / 1e9 / peak, 4) if t_sl > 0 else None},
         "tuning": {"tile_x": args.tile_x or "default", "tile_y": args.tile_y or "default",
-                   "zseg": args.zseg or "default"},
-        "gpu_launches": int(args.steps * (window * (5 if upml_nodes else 4) + 2)),
+                   "zseg": args.zseg or "default", "depth": depth, "pair_zseg": args.pair_zseg or "default"},
+        "gpu_launches": int(args.steps * (singles * (5 if upml_nodes else 4) + pairs * (9 if upml_nodes else 7) + 2)),
         "clocks": clk.summary(),
         "e2e": e2e,
         "device_ms_in_timed_region": round(dev_ms, 3),
@@ -538,6 +546,8 @@ def main():
     ap.add_argument("--tile-x", type=int, default=0, help="fused tile width (62 or 124 columns); 0 = tuned default")
     ap.add_argument("--tile-y", type=int, default=0, help="fused tile height (4 or 8 rows); 0 = tuned default")
     ap.add_argument("--zseg", type=int, default=0, help="fused z-segment length; 0 = tuned default")
+    ap.add_argument("--depth", type=int, default=0, help="leapfrog steps per interior pass (1 or 2); 0 = default")
+    ap.add_argument("--pair-zseg", type=int, default=0, help="z-segment length of the two-step pass; 0 = default")
     ap.add_argument("--no-batched", action="store_true", help="default run: skip the batched sub-record")
     ap.add_argument("--no-served", action="store_true", help="default run: skip the served sub-records")
     ap.add_argument("--sub-requests", type=int, default=24, help="default run: requests of the served sub-record")

@@ -100,6 +100,7 @@ typedef struct {
     int n_combo;               /* distinct per-node E-coefficient triples */
     long long slab_aux_values; /* auxiliary D~/B~ values held by the slabs (read and written once per step) */
     int pitch;                 /* row pitch of the device field and id arrays, elements (nx + 1 rounded up) */
+    int depth;                 /* leapfrog steps per interior pass in effect: 1, or 2 (time blocking) */
 } fdtd_info_t;
 
 /* Create a board (Model section, Fig. 1).
@@ -381,11 +382,25 @@ void fdtd_batch_destroy(fdtd_batch *b);
  * or 8; a 62x8 tile is worked by four compute warps of 2 rows, a 124x8 tile
  * by two warps of 4 rows per strip; default 62x8), the z-segment length
  * (planes one tile marches before the next work item; default 10) and the
- * number of steps per CUDA graph (default 16).  Values <= 0 keep the current
+ * number of steps per CUDA graph (default 16).  depth is the number of
+ * leapfrog steps one sweep over the interior region advances (time blocking,
+ * Model section: the leapfrog's H and E updates of two steps in one pass):
+ * 1 (default) or 2.  With depth 2 a single board keeps a third field set
+ * (6 x nodes more field values) and runs pairs of steps as one two-step
+ * interior pass plus the slab, z-UPML and source launches of both steps.
+ * With FP32 storage the results are bit-identical to depth 1.  With FP16
+ * storage the E update of the interior region's one-node outer layer reads
+ * the stored (FP16) H~ where depth 1 uses the unrounded value, a difference at
+ * the storage rounding level.  Depth 2 takes effect on boards
+ * whose interior spans at least 3 nodes per axis, whose fused region starts
+ * at an even x, and whose top wall is a z-UPML or PEC (fdtd_info reports the
+ * depth in effect); batches run depth 1.  pair_zseg is the z-segment length
+ * of the two-step pass (default 38, >= 2).  Values <= 0 keep the current
  * setting; unsupported tiles are rejected with FDTD_EINVAL.  Applies to
  * launches queued afterwards. */
 typedef struct {
     int tile_x, tile_y, zseg, graph_chunk;
+    int depth, pair_zseg;
 } fdtd_tuning;
 
 int fdtd_set_tuning(fdtd_ctx *ctx, const fdtd_tuning *t);

@@ -42,11 +42,12 @@ class fdtd_info_t(ctypes.Structure):
                 ("precision", c_int), ("interior_nodes", c_longlong), ("fused_upml_nodes", c_longlong),
                 ("slab_nodes", c_longlong),
                 ("device_bytes", c_longlong), ("n_combo", c_int), ("slab_aux_values", c_longlong),
-                ("pitch", c_int)]
+                ("pitch", c_int), ("depth", c_int)]
 
 
 class fdtd_tuning(ctypes.Structure):
-    _fields_ = [("tile_x", c_int), ("tile_y", c_int), ("zseg", c_int), ("graph_chunk", c_int)]
+    _fields_ = [("tile_x", c_int), ("tile_y", c_int), ("zseg", c_int), ("graph_chunk", c_int),
+                ("depth", c_int), ("pair_zseg", c_int)]
 
 
 class FdtdError(RuntimeError):

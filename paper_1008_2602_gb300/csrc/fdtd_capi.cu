@@ -96,13 +96,16 @@ struct fdtd_ctx {
     long long host_step = 0;
     fdtd_batch *batch = nullptr;
     // single-board plan and graph
-    fdtd_tuning tune{62, 8, 10, 16};
+    fdtd_tuning tune{62, 8, 10, 16, 1, 38};
     bool plan_dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;   // device [0]=board ptr, then prefixes
     size_t plan_cap = 0;
     cudaGraphExec_t graph = nullptr;
     int graph_chunk = 0;
+    cudaGraphExec_t graph2 = nullptr;   // pairs of steps (depth 2)
+    int graph2_chunk = 0;
+    size_t fbytes = 0;                  // bytes of one field component
     double *energy_buf = nullptr;    // partials + 2 outputs
     int energy_n = 0;
     int grid_cap = 0;
@@ -117,7 +120,7 @@ struct fdtd_batch {
     bool own_stream = false;
     std::vector<fdtd_ctx *> members;
     std::vector<long long> remaining;
-    fdtd_tuning tune{62, 8, 10, 16};
+    fdtd_tuning tune{62, 8, 10, 16, 1, 38};
     bool dirty = true;
     Plan plan{};
     long long *plan_buf = nullptr;
@@ -330,6 +333,41 @@ bool layout_board(const fdtd_grid &g, const fdtd_boundary &bnd, const Axes &A, B
         zplanes[bx] = fused && planes > 0 ? planes : 0;
     }
     return true;
+}
+
+// Band boxes of the two-step pass: the one-node outer layer of the interior
+// region I whose second step needs the slab kernels' intermediate state.  H+E
+// boxes (high x face, high y face) first, then E-only boxes (low x face, low y
+// face, bottom plane); disjoint, blocks numbered after the slab blocks.
+void layout_band(Board &h)
+{
+    h.n_band = h.n_band_h = 0;
+    h.band_blocks = h.band_h_blocks = 0;
+    if (h.ix1 - h.ix0 < 3 || h.iy1 - h.iy0 < 3 || h.iz1 - h.iz0 < 3) return;
+    const int ix0 = h.ix0, ix1 = h.ix1, iy0 = h.iy0, iy1 = h.iy1, iz0 = h.iz0, iz1 = h.iz1;
+    const int boxes[5][6] = {{ix1 - 1, ix1, iy0, iy1, iz0, iz1},
+                             {ix0, ix1 - 1, iy1 - 1, iy1, iz0, iz1},
+                             {ix0, ix0 + 1, iy0, iy1 - 1, iz0, iz1},
+                             {ix0 + 1, ix1 - 1, iy0, iy0 + 1, iz0, iz1},
+                             {ix0 + 1, ix1 - 1, iy0 + 1, iy1 - 1, iz0, iz0 + 1}};
+    if (h.n_slab + 5 > kMaxSlab) return;
+    int blocks = h.slab_blocks;
+    for (int b = 0; b < 5; ++b) {
+        Slab &sl = h.slab[h.n_slab + b];
+        sl.i0 = boxes[b][0]; sl.i1 = boxes[b][1]; sl.j0 = boxes[b][2]; sl.j1 = boxes[b][3];
+        sl.k0 = boxes[b][4]; sl.k1 = boxes[b][5];
+        sl.ni = sl.i1 - sl.i0; sl.nj = sl.j1 - sl.j0;
+        sl.n = (long long)sl.ni * sl.nj * (sl.k1 - sl.k0);
+        sl.block0 = blocks;
+        for (int a = 0; a < 6; ++a) sl.aux[a] = nullptr;
+        const long long cols = sl.k1 - sl.k0 == 1 ? (long long)sl.ni * ((sl.nj + kSlabKz - 1) / kSlabKz)
+                                                  : (long long)sl.ni * sl.nj * ((sl.k1 - sl.k0 + kSlabKz - 1) / kSlabKz);
+        blocks += (int)((cols + kSlabThreads - 1) / kSlabThreads);
+        if (b == 1) h.band_h_blocks = blocks - h.slab_blocks;
+    }
+    h.band_blocks = blocks - h.slab_blocks;
+    h.n_band = 5;
+    h.n_band_h = 2;
 }
 
 // Per-node coefficient ids: ce = 1/eps_r(edge) for the three edges starting at
@@ -684,11 +722,23 @@ int encode_maps(fdtd_ctx *c, int tx, int ty)
                                                          : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     const int es = elem_size(c->prec);
     const uint64_t d0 = h.pitch, d1 = h.ny + 1, d2 = h.nz + 1;
-    for (int par = 0; par < 2; ++par)
-        for (int comp = 0; comp < 3; ++comp) {
-            if (int r = encode3d(&maps[tm_e(par, comp)], fdt, es, h.f[par][comp], d0, d1, d2, box_e(tx), ty + 2)) return r;
-            if (int r = encode3d(&maps[tm_h(par, comp)], fdt, es, h.f[par][3 + comp], d0, d1, d2, box_h(tx), ty + 1)) return r;
+    for (int set = 0; set < 3; ++set)
+        for (int comp = 0; comp < 3 && h.f[set][0]; ++comp) {
+            if (int r = encode3d(&maps[tm_e(set, comp)], fdt, es, h.f[set][comp], d0, d1, d2, box_e(tx), ty + 2)) return r;
+            if (int r = encode3d(&maps[tm_h(set, comp)], fdt, es, h.f[set][3 + comp], d0, d1, d2, box_h(tx), ty + 1)) return r;
         }
+    if (h.f[2][0]) {   // two-step pass: 60 x 8 tiles, boxes of kPairEW columns
+        for (int set = 0; set < 2; ++set)
+            for (int comp = 0; comp < 3; ++comp) {
+                if (int r = encode3d(&maps[tp_e(set, comp)], fdt, es, h.f[set][comp], d0, d1, d2, kPairEW, kPairRows + 4)) return r;
+                if (int r = encode3d(&maps[tp_h(set, comp)], fdt, es, h.f[set][3 + comp], d0, d1, d2, kPairEW, kPairRows + 3)) return r;
+            }
+        for (int comp = 0; comp < 3; ++comp)
+            if (int r = encode3d(&maps[tp_t(comp)], fdt, es, h.f[2][comp], d0, d1, d2, kPairEW, kPairRows + 2)) return r;
+        if (int r = encode3d(&maps[kTpCid], h.id16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
+                             h.id16 ? 2 : 1, h.cid, d0, d1, d2, h.id16 ? kPairC16W : kPairC8W, kPairRows + 2))
+            return r;
+    }
     if (int r = encode3d(&maps[kTmCid], h.id16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8,
                          h.id16 ? 2 : 1, h.cid, d0, d1, d2, h.id16 ? box_c16(tx) : box_c8(tx), ty))
         return r;
@@ -726,6 +776,14 @@ long long fused_items(const Board &h, const fdtd_tuning &t, bool zp)
     return ((Lx + t.tile_x - 1) / t.tile_x) * ((Ly + t.tile_y - 1) / t.tile_y) * nseg;
 }
 
+// Two-step items of a board: 60 x 8 tiles x z segments of pair_zseg planes of I.
+long long pair_items(const Board &h, const fdtd_tuning &t)
+{
+    if (!h.pair_ok) return 0;
+    const long long Lx = h.ix1 - h.ix0, Ly = h.iy1 - h.iy0, Lz = h.iz1 - h.iz0;
+    return ((Lx + kPairCols - 1) / kPairCols) * ((Ly + kPairRows - 1) / kPairRows) * ((Lz + t.pair_zseg - 1) / t.pair_zseg);
+}
+
 long long dft_items(const Board &h)
 {
     if (h.n_total <= 0 || h.n_probe <= 0) return 0;
@@ -745,13 +803,22 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
                                          "); nothing was launched");
     long long n_slab_blk = 0;
     for (int b = 0; b < nb; ++b) n_slab_blk += boards[b]->h.slab_blocks;
+    // a single board's band blocks follow its slab blocks (second step of a pair)
+    const bool band = nb == 1 && boards[0]->h.pair_ok && boards[0]->h.n_band > 0;
+    if (band) n_slab_blk += boards[0]->h.band_blocks;
     static_assert(sizeof(SlabBlock) == 4 * sizeof(long long), "slab block descriptor layout");
-    const size_t head = ((size_t)nb + 4 * ((size_t)nb + 1) + 1 + 1) & ~(size_t)1;   // + two work counters, 16-byte aligned
+    const size_t head = ((size_t)nb + 4 * ((size_t)nb + 1) + 2 + 1) & ~(size_t)1;   // + four work counters, 16-byte aligned
     const size_t words = head + 4 * (size_t)n_slab_blk;
     host.assign(words, 0);
     long long *ptrs = host.data();
     long long *ip = ptrs + nb, *zp = ip + nb + 1, *sp = zp + nb + 1, *dp = sp + nb + 1;
     SlabBlock *sb = reinterpret_cast<SlabBlock *>(ptrs + head);
+    // a single board's band blocks come first in the table, E-only boxes then
+    // H+E boxes, so that a second-step launch starts them before the slab
+    // blocks (their threads march single columns; at the end they would add
+    // their latency to the launch)
+    const long long nbb = band ? boards[0]->h.band_blocks : 0;
+    const long long nbh = band ? boards[0]->h.band_h_blocks : 0;
     for (int b = 0; b < nb; ++b) {
         const Board &h = boards[b]->h;
         ptrs[b] = (long long)(uintptr_t)boards[b]->d;
@@ -759,10 +826,16 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
         zp[b + 1] = zp[b] + fused_items(h, t, true);
         sp[b + 1] = sp[b] + h.slab_blocks;
         dp[b + 1] = dp[b] + dft_items(h);
-        for (int s = 0; s < h.n_slab; ++s) {
-            const int end = s + 1 < h.n_slab ? (int)h.slab[s + 1].block0 : h.slab_blocks;
+        const int ns = h.n_slab + (band ? h.n_band : 0);
+        for (int s = 0; s < ns; ++s) {
+            const int end = s + 1 < ns ? (int)h.slab[s + 1].block0 : h.slab_blocks + (band ? h.band_blocks : 0);
             for (int k = (int)h.slab[s].block0; k < end; ++k) {
-                SlabBlock &e = sb[sp[b] + k];
+                // table position: slab blocks after the band; band H+E blocks
+                // (numbered first) after the E-only ones
+                long long at = sp[b] + k + nbb;
+                if (band && k >= h.slab_blocks) at = k - h.slab_blocks < nbh ? (nbb - nbh) + (k - h.slab_blocks)
+                                                                              : k - h.slab_blocks - nbh;
+                SlabBlock &e = sb[at];
                 e.B = boards[b]->d;
                 e.step = h.step;
                 e.stop = h.stop;
@@ -797,7 +870,12 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.n_slab = sp[nb];
     plan.n_dft = dp[nb];
     plan.work = (int *)(buf + nb + 4 * (nb + 1));
-    plan.slab_blk = reinterpret_cast<const SlabBlock *>(buf + head);
+    plan.slab_blk = reinterpret_cast<const SlabBlock *>(buf + head) + nbb;
+    plan.pair_zseg = t.pair_zseg;
+    plan.n_pair = band ? pair_items(boards[0]->h, t) : 0;
+    plan.first_of_pair = 0;
+    plan.n_band_h = band ? boards[0]->h.band_h_blocks : 0;
+    plan.n_band = band ? boards[0]->h.band_blocks : 0;
     return FDTD_OK;
 }
 
@@ -838,6 +916,97 @@ int run_steps(const Plan &plan, int prec, int grid_cap, int n, int chunk, cudaGr
         for (int s = 0; s < n; ++s) CK(launch_step(plan, prec, grid_cap, st));
         CK(launch_dft(plan, grid_cap, st));
     }
+    return FDTD_OK;
+}
+
+// Run n steps of a depth-2 single-board plan: a single step to reach an even
+// step, then pairs (CUDA graphs of chunk / 2 pairs), then one or two single
+// steps, so that the states after the last two steps are complete in memory
+// (the state in the middle of a pair is kept only where later launches read
+// it).
+int run_depth2(const Plan &plan, int prec, int grid_cap, long long step, int n, int chunk, cudaGraphExec_t &graph2,
+               int &graph2_chunk, cudaStream_t st)
+{
+    if (n <= 0) return FDTD_OK;
+    NvtxRange range("fdtd step pairs");
+    int left = n;
+    bool direct = false;
+    if (step & 1) {
+        CK(launch_step(plan, prec, grid_cap, st));
+        --left;
+        direct = true;
+    }
+    int pairs = left >= 3 ? (left - 1) / 2 : 0;
+    left -= 2 * pairs;
+    const int cp = std::max(1, chunk / 2);
+    if (cp > 1 && pairs >= cp) {
+        if (!graph2 || graph2_chunk != cp) {
+            if (graph2) cudaGraphExecDestroy(graph2);
+            graph2 = nullptr;
+            cudaGraph_t gr = nullptr;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = cudaSuccess;
+            for (int s = 0; s < cp && e == cudaSuccess; ++s) e = launch_pair(plan, prec, grid_cap, st);
+            if (e == cudaSuccess) e = launch_dft(plan, grid_cap, st);
+            cudaError_t e2 = cudaStreamEndCapture(st, &gr);
+            if (e != cudaSuccess) { if (gr) cudaGraphDestroy(gr); return cuda_fail(e, "capture"); }
+            if (e2 != cudaSuccess) return cuda_fail(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&graph2, gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) { graph2 = nullptr; return cuda_fail(e, "cudaGraphInstantiate"); }
+            graph2_chunk = cp;
+        }
+        for (int r = 0; r < pairs / cp; ++r) CK(cudaGraphLaunch(graph2, st));
+        pairs %= cp;
+    }
+    for (int p = 0; p < pairs; ++p) CK(launch_pair(plan, prec, grid_cap, st));
+    for (int s = 0; s < left; ++s) CK(launch_step(plan, prec, grid_cap, st));
+    if (direct || pairs > 0 || left > 0) CK(launch_dft(plan, grid_cap, st));
+    return FDTD_OK;
+}
+
+// Whether the two-step pass can run on this board (set 2 allocated).  The
+// plane above I must be written before the pass by the z-UPML launch, or be
+// the zero plane behind a PEC wall; x of the tiles' lane pairs must be even.
+bool pair_possible(const fdtd_ctx *c)
+{
+    const Board &h = c->h;
+    return h.ix1 > h.ix0 && h.iy1 > h.iy0 && (h.ix0 % 2) == 0 && h.ix1 - h.ix0 >= 3 && h.iy1 - h.iy0 >= 3 &&
+           h.iz1 - h.iz0 >= 3 && h.n_band == 5 && (c->bnd.depth[5] > 0 || c->bnd.wall[5] == FDTD_WALL_PEC);
+}
+
+// Field sets for depth d: set 2 is allocated on first use, and the sets are
+// renamed so that the states after the last two steps sit where set_of(d, .)
+// expects them.
+int set_time_depth(fdtd_ctx *c, int d)
+{
+    Board &h = c->h;
+    const int old = h.tdepth;
+    if (d == 2 && !h.f[2][0]) {
+        unsigned char *blk = nullptr;
+        if (int r = dalloc(c, &blk, 6 * c->fbytes)) return r;
+        CK(cudaMemsetAsync(blk, 0, 6 * c->fbytes, c->cur));
+        for (int f = 0; f < 6; ++f) h.f[2][f] = blk + f * c->fbytes;
+    }
+    CK(cudaStreamSynchronize(c->cur));
+    if (d != old) {
+        const long long n = c->host_step;
+        const int a = set_of(old, n), b = set_of(old, n - 1), x = set_of(d, n), y = set_of(d, n - 1);
+        void *f[3][6];
+        bool used[3] = {false, false, false};
+        for (int q = 0; q < 6; ++q) { f[x][q] = h.f[a][q]; f[y][q] = h.f[b][q]; }
+        used[a] = used[b] = true;
+        int spare = 0;
+        while (spare < 3 && used[spare]) ++spare;
+        const int z = 3 - x - y;
+        for (int q = 0; q < 6; ++q) f[z][q] = spare < 3 ? h.f[spare][q] : nullptr;
+        std::memcpy(h.f, f, sizeof(f));
+        h.tdepth = d;
+        h.tm_tx = 0;   // the tensor maps name the sets' addresses
+        c->plan_dirty = true;
+    }
+    h.pair_ok = (d == 2 && h.f[2][0] && pair_possible(c)) ? 1 : 0;
+    if (c->d) return upload_board(c);
     return FDTD_OK;
 }
 
@@ -1019,7 +1188,11 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
 
     int r = FDTD_OK;
     const size_t fbytes = (size_t)h.nodes * elem_size(precision);
-    // the six components of one parity are contiguous (component stride = nodes)
+    c->fbytes = fbytes;
+    h.tdepth = 1;
+    h.pair_ok = 0;
+    for (int f = 0; f < 6; ++f) h.f[2][f] = nullptr;   // set 2: allocated when two-step passes are enabled
+    // the six components of one set are contiguous (component stride = nodes)
     for (int p = 0; p < 2 && !r; ++p) {
         unsigned char *blk = nullptr;
         r = dalloc(c, &blk, 6 * fbytes);
@@ -1051,6 +1224,7 @@ int fdtd_create(const fdtd_grid *grid, const uint8_t *mat_ids, const double *eps
     // fused region and slab boxes
     bool aux[kMaxSlab][6];
     if (!layout_board(*grid, *bnd, A, h, aux, c->zplanes)) { fdtd_destroy(c); return fail(FDTD_EINVAL, "internal: too many slab boxes"); }
+    layout_band(h);
     for (int s = 0; s < h.n_slab && !r; ++s) {
         Slab &sl = h.slab[s];
         for (int comp = 0; comp < 6 && !r; ++comp) {
@@ -1113,6 +1287,7 @@ int fdtd_set_source(fdtd_ctx *c, int i, int j, int k, int comp, double J0, doubl
     Source S{};
     S.node = node_index(c->h, i, j, k);
     S.comp = comp;
+    S.i = i; S.j = j; S.k = k;
     S.J0 = J0; S.t0 = t0; S.tau = tau;
     S.coef = (double)ce * c->dt / kEps0;
     c->src.push_back(S);
@@ -1153,6 +1328,7 @@ int fdtd_set_voltage_source(fdtd_ctx *c, int i, int j, int k, int comp, double V
     Source S{};
     S.node = node_index(c->h, i, j, k);
     S.comp = comp;
+    S.i = i; S.j = j; S.k = k;
     S.kind = kSrcResistiveVoltage;
     S.J0 = V0; S.t0 = t0; S.tau = tau;
     S.rs = Rs;
@@ -1170,6 +1346,7 @@ int fdtd_add_probe(fdtd_ctx *c, int i, int j, int k, int comp, int *probe_id)
     Probe p{};
     p.node = node_index(c->h, i, j, k);
     p.comp = comp;
+    p.i = i; p.j = j; p.k = k;
     c->probe.push_back(p);
     if (probe_id) *probe_id = (int)c->probe.size() - 1;
     return FDTD_OK;
@@ -1196,8 +1373,14 @@ int fdtd_set_tuning(fdtd_ctx *c, const fdtd_tuning *t)
     if (t->tile_y > 0) n.tile_y = t->tile_y;
     if (t->zseg > 0) n.zseg = t->zseg;
     if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
+    if (t->depth > 0) n.depth = t->depth;
+    if (t->pair_zseg > 0) n.pair_zseg = t->pair_zseg;
     if (!fused_tile_supported(n.tile_x, n.tile_y))
         return fail(FDTD_EINVAL, "fused tile (tile_x x tile_y) must be 62x4, 62x8, 124x4 or 124x8");
+    if (n.depth != 1 && n.depth != 2) return fail(FDTD_EINVAL, "depth must be 1 or 2");
+    if (n.pair_zseg < 2) return fail(FDTD_EINVAL, "pair_zseg must be >= 2");
+    if (n.depth != c->h.tdepth)
+        if (int r = set_time_depth(c, n.depth)) return r;
     c->tune = n;
     c->plan_dirty = true;
     return FDTD_OK;
@@ -1211,8 +1394,13 @@ int fdtd_step(fdtd_ctx *c, int n)
     if (n < 0) return fail(FDTD_EINVAL, "n must be >= 0");
     if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; step the batch");
     if (int r = prepare_single(c)) return r;
-    if (int r = run_steps(c->plan, c->prec, c->grid_cap, n, c->tune.graph_chunk, c->graph, c->graph_chunk, c->cur))
+    if (c->h.pair_ok) {
+        if (int r = run_depth2(c->plan, c->prec, c->grid_cap, c->host_step, n, c->tune.graph_chunk, c->graph2,
+                               c->graph2_chunk, c->cur))
+            return r;
+    } else if (int r = run_steps(c->plan, c->prec, c->grid_cap, n, c->tune.graph_chunk, c->graph, c->graph_chunk, c->cur)) {
         return r;
+    }
     c->host_step += n;
     return FDTD_OK;
 }
@@ -1227,6 +1415,7 @@ static int prepare_single(fdtd_ctx *c)
         if (int r = build_plan(one, c->tune, c->plan_buf, c->plan_cap, c->plan, c->cur, host)) return r;
         CK(cudaStreamSynchronize(c->cur));
         if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        if (c->graph2) { cudaGraphExecDestroy(c->graph2); c->graph2 = nullptr; }
         c->plan_dirty = false;
     }
     return FDTD_OK;
@@ -1238,19 +1427,35 @@ int fdtd_step_profiled(fdtd_ctx *c, int n, double *phase_ms)
     if (n < 0) return fail(FDTD_EINVAL, "n must be >= 0");
     if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; step the batch");
     if (int r = prepare_single(c)) return r;
-    const size_t need = (size_t)n * (kNumPhases + 1) + 2;
+    const size_t need = (size_t)n * (kPairLaunches + 1) + 2;
     while (c->events.size() < need) {
         cudaEvent_t e;
         CK(cudaEventCreate(&e));
         c->events.push_back(e);
     }
     for (int p = 0; p <= kNumPhases; ++p) phase_ms[p] = 0.0;
+    // the launch sequence: single steps (five launches) and, with depth 2,
+    // pairs (nine launches); the same split as fdtd_step
+    std::vector<int> unit;   // 1: single step, 2: pair
+    {
+        long long s = c->host_step;
+        int left = n;
+        if (c->h.pair_ok && (s & 1) && left > 0) { unit.push_back(1); --left; }
+        int pairs = c->h.pair_ok && left >= 3 ? (left - 1) / 2 : 0;
+        for (int p = 0; p < pairs; ++p) unit.push_back(2);
+        left -= 2 * pairs;
+        for (int q = 0; q < left; ++q) unit.push_back(1);
+    }
+    std::vector<int> phase_of;   // phase of each timed launch
     size_t ev = 0;
-    for (int s = 0; s < n; ++s) {
+    for (int u : unit) {
         CK(cudaEventRecord(c->events[ev++], c->cur));
-        for (int ph = 0; ph < kNumPhases; ++ph) {
-            CK(launch_phase(c->plan, c->prec, ph, c->grid_cap, c->cur));
+        const int nl = u == 2 ? kPairLaunches : kNumPhases;
+        for (int i = 0; i < nl; ++i) {
+            if (u == 2) CK(launch_pair_part(c->plan, c->prec, i, c->grid_cap, c->cur));
+            else CK(launch_phase(c->plan, c->prec, i, c->grid_cap, c->cur));
             CK(cudaEventRecord(c->events[ev++], c->cur));
+            phase_of.push_back(u == 2 ? kPairPhase[i] : i);
         }
     }
     CK(cudaEventRecord(c->events[ev++], c->cur));
@@ -1258,13 +1463,15 @@ int fdtd_step_profiled(fdtd_ctx *c, int n, double *phase_ms)
     CK(cudaEventRecord(c->events[ev++], c->cur));
     CK(cudaStreamSynchronize(c->cur));
     ev = 0;
-    for (int s = 0; s < n; ++s) {
-        for (int ph = 0; ph < kNumPhases; ++ph) {
+    size_t li = 0;
+    for (int u : unit) {
+        const int nl = u == 2 ? kPairLaunches : kNumPhases;
+        for (int i = 0; i < nl; ++i) {
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, c->events[ev + ph], c->events[ev + ph + 1]));
-            phase_ms[ph] += ms;
+            CK(cudaEventElapsedTime(&ms, c->events[ev + i], c->events[ev + i + 1]));
+            phase_ms[phase_of[li++]] += ms;
         }
-        ev += kNumPhases + 1;
+        ev += nl + 1;
     }
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, c->events[ev], c->events[ev + 1]));
@@ -1311,7 +1518,7 @@ int fdtd_get_field(fdtd_ctx *c, int field, float *out)
     if (field < 0 || field > 5) return fail(FDTD_EINVAL, "field must be 0..5");
     if (int r = fdtd_sync(c)) return r;
     const Board &h = c->h;
-    const int par = (int)(c->host_step & 1);
+    const int par = set_of(h.tdepth, c->host_step);
     const int es = elem_size(c->prec);
     std::vector<unsigned char> buf((size_t)h.nodes * es);
     CK(cudaMemcpy(buf.data(), h.f[par][field], buf.size(), cudaMemcpyDeviceToHost));
@@ -1336,7 +1543,7 @@ int fdtd_get_plane(fdtd_ctx *c, int field, int k, float *out)
     if (k < 0 || k > c->h.nz) return fail(FDTD_EINVAL, "plane index out of range");
     if (int r = fdtd_sync(c)) return r;
     const Board &h = c->h;
-    const int par = (int)(c->host_step & 1);
+    const int par = set_of(h.tdepth, c->host_step);
     const int es = elem_size(c->prec);
     const int NX = h.nx + 1, NY = h.ny + 1;
     std::vector<unsigned char> buf((size_t)NX * NY * es);
@@ -1372,8 +1579,9 @@ int fdtd_reset(fdtd_ctx *c)
     if (!c) return fail(FDTD_EINVAL, "NULL context");
     Board &h = c->h;
     const size_t fbytes = (size_t)h.nodes * elem_size(c->prec);
-    for (int p = 0; p < 2; ++p)
-        for (int f = 0; f < 6; ++f) CK(cudaMemsetAsync(h.f[p][f], 0, fbytes, c->cur));
+    for (int p = 0; p < 3; ++p)
+        for (int f = 0; f < 6; ++f)
+            if (h.f[p][f]) CK(cudaMemsetAsync(h.f[p][f], 0, fbytes, c->cur));
     for (int s = 0; s < h.n_slab; ++s)
         for (int a = 0; a < 6; ++a)
             if (h.slab[s].aux[a]) CK(cudaMemsetAsync(h.slab[s].aux[a], 0, sizeof(float) * (size_t)h.slab[s].n, c->cur));
@@ -1405,12 +1613,14 @@ struct CkptHeader {
 };
 constexpr uint64_t kCkptMagic = 0x31544b43445446ull;   // "FDTDCKT1"
 
-// Device regions of the state, in checkpoint order.
-void ckpt_regions(const fdtd_ctx *c, std::vector<std::pair<void *, size_t>> &out)
+// Device regions of the state after `step` steps, in checkpoint order: the
+// field sets holding the states after steps n and n - 1 (in that order,
+// whichever sets they occupy), then the auxiliaries, trace and DFT.
+void ckpt_regions(const fdtd_ctx *c, long long step, std::vector<std::pair<void *, size_t>> &out)
 {
     const Board &h = c->h;
     const size_t fbytes = (size_t)h.nodes * elem_size(c->prec);
-    for (int p = 0; p < 2; ++p)
+    for (int p : {set_of(h.tdepth, step), set_of(h.tdepth, step - 1)})
         for (int f = 0; f < 6; ++f) out.push_back({h.f[p][f], fbytes});
     for (int s = 0; s < h.n_slab; ++s)
         for (int a = 0; a < 6; ++a)
@@ -1429,7 +1639,7 @@ CkptHeader ckpt_header(const fdtd_ctx *c)
     const Board &h = c->h;
     CkptHeader H{};
     H.magic = kCkptMagic;
-    H.version = 1;
+    H.version = 2;
     H.nx = h.nx; H.ny = h.ny; H.nz = h.nz; H.pitch = h.pitch; H.prec = c->prec;
     H.n_probe = (int)c->probe.size(); H.n_src = (int)c->src.size();
     H.n_total = h.n_total; H.n_bins = h.n_bins; H.n_slab = h.n_slab;
@@ -1447,7 +1657,8 @@ int fdtd_save(fdtd_ctx *c, void *buf, size_t cap, size_t *size)
     if (c->batch) return fail(FDTD_ESTATE, "context is in a batch; remove it first");
     if (int r = finalize(c)) return r;
     std::vector<std::pair<void *, size_t>> reg;
-    ckpt_regions(c, reg);
+    CK(cudaStreamSynchronize(c->cur));
+    ckpt_regions(c, c->host_step, reg);
     size_t need = sizeof(CkptHeader);
     for (auto &g : reg) need += g.second;
     *size = need;
@@ -1484,7 +1695,7 @@ int fdtd_load(fdtd_ctx *c, const void *buf, size_t size)
         return fail(FDTD_EINVAL, "checkpoint belongs to a different board or settings");
     if (H.step < 0 || H.dft_done < 0 || H.dft_done > H.step) return fail(FDTD_EINVAL, "corrupt checkpoint counters");
     std::vector<std::pair<void *, size_t>> reg;
-    ckpt_regions(c, reg);
+    ckpt_regions(c, H.step, reg);
     size_t need = sizeof(CkptHeader);
     for (auto &g : reg) need += g.second;
     if (size != need) return fail(FDTD_EINVAL, "checkpoint size does not match this board");
@@ -1557,7 +1768,7 @@ int fdtd_halo_pack(fdtd_ctx *c, int axis, int plane, unsigned comp_mask, void *d
     if (!dev_buf) return fail(FDTD_EINVAL, "NULL buffer");
     if (int r = finalize(c)) return r;
     const size_t es = elem_size(c->prec);
-    const int par = (int)(c->host_step & 1);
+    const int par = set_of(c->h.tdepth, c->host_step);
     unsigned char *o = static_cast<unsigned char *>(dev_buf);
     for (int f = 0; f < 6; ++f) {
         if (!(comp_mask & (1u << f))) continue;
@@ -1576,7 +1787,7 @@ int fdtd_halo_unpack(fdtd_ctx *c, int axis, int plane, unsigned comp_mask, const
     if (!dev_buf) return fail(FDTD_EINVAL, "NULL buffer");
     if (int r = finalize(c)) return r;
     const size_t es = elem_size(c->prec);
-    const int par = (int)(c->host_step & 1);
+    const int par = set_of(c->h.tdepth, c->host_step);
     const unsigned char *in = static_cast<const unsigned char *>(dev_buf);
     for (int f = 0; f < 6; ++f) {
         if (!(comp_mask & (1u << f))) continue;
@@ -1609,14 +1820,14 @@ int fdtd_halo_copy(fdtd_ctx *dst, int dst_plane, fdtd_ctx *src, int src_plane, i
     cudaEventDestroy(ev);
     if (e != cudaSuccess) return cuda_fail(e, "halo copy ordering");
     const size_t es = elem_size(dst->prec);
-    const int par = (int)(dst->host_step & 1);
+    const int spar = set_of(src->h.tdepth, src->host_step), dpar = set_of(dst->h.tdepth, dst->host_step);
     for (int f = 0; f < 6; ++f) {
         if (!(comp_mask & (1u << f))) continue;
         cudaMemcpy3DPeerParms p{};
-        p.srcPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(src->h.f[par][f]) + gs.off * es, gs.spitch * es,
+        p.srcPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(src->h.f[spar][f]) + gs.off * es, gs.spitch * es,
                                        gs.width * es, gs.height);
         p.srcDevice = src->device;
-        p.dstPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(dst->h.f[par][f]) + gd.off * es, gd.spitch * es,
+        p.dstPtr = make_cudaPitchedPtr(static_cast<unsigned char *>(dst->h.f[dpar][f]) + gd.off * es, gd.spitch * es,
                                        gd.width * es, gd.height);
         p.dstDevice = dst->device;
         p.extent = make_cudaExtent(gs.width * es, gs.height, 1);
@@ -1767,6 +1978,7 @@ int fdtd_info(fdtd_ctx *c, fdtd_info_t *info)
     info->slab_nodes = sn;
     info->slab_aux_values = sa;
     info->pitch = h.pitch;
+    info->depth = h.pair_ok ? 2 : 1;
     info->device_bytes = c->device_bytes;
     info->n_combo = c->n_combo;
     return FDTD_OK;
@@ -1778,6 +1990,7 @@ void fdtd_destroy(fdtd_ctx *c)
     if (c->batch) fdtd_batch_remove(c->batch, c);
     if (c->cur) cudaStreamSynchronize(c->cur);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph2) cudaGraphExecDestroy(c->graph2);
     if (c->plan_buf) cudaFree(c->plan_buf);
     for (cudaEvent_t e : c->events) cudaEventDestroy(e);
     for (void *p : c->allocs) cudaFree(p);
@@ -1812,6 +2025,7 @@ int fdtd_batch_set_tuning(fdtd_batch *b, const fdtd_tuning *t)
     if (t->tile_y > 0) n.tile_y = t->tile_y;
     if (t->zseg > 0) n.zseg = t->zseg;
     if (t->graph_chunk > 0) n.graph_chunk = t->graph_chunk;
+    if (t->depth > 1) return fail(FDTD_EINVAL, "a batch steps one leapfrog step per launch set (depth 1)");
     if (!fused_tile_supported(n.tile_x, n.tile_y))
         return fail(FDTD_EINVAL, "fused tile (tile_x x tile_y) must be 62x4, 62x8, 124x4 or 124x8");
     b->tune = n;

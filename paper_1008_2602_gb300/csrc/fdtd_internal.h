@@ -15,7 +15,8 @@
 // Memory layout in HBM: every field component is a [nz+1][ny+1][pitch] array
 // (x fastest, pitch an odd multiple of 32 elements, see row_pitch),
 // indexed by the node its Yee sample starts at; samples that do not exist stay
-// zero.  Fields are ping-ponged: step n reads parity n&1, writes the other.
+// zero.  Fields live in two or three sets: a step reads the set holding the
+// current state and writes another (see set_of).
 // One uint8 per node (uint16 when a geometry has more than 256) selects a row
 // (ce_x, ce_y, ce_z) = 1/eps_r of its three E edges (0 on PEC) of a table.
 // UPML factors are 1D per axis at integer and half positions.
@@ -48,7 +49,7 @@
 
 namespace fdtd {
 
-constexpr int kMaxSlab = 26;
+constexpr int kMaxSlab = 32;
 // Row pitch of the field, id and diagnostic arrays (elements): nx + 1 rounded
 // up to a multiple of 32, then to an odd multiple of 32, so that FP32 rows
 // start 128-byte aligned and span an odd number of 128-byte lines (consecutive
@@ -86,6 +87,7 @@ struct Source {
     long long node;               // linear node index
     int comp;                     // 0..2
     int kind;                     // SourceKind
+    int i, j, k, pad;             // the node
     double J0, t0, tau;           // Eq. 8 pulse (amplitude J0 [A/m^2], or V0 [V] for a voltage source)
     double coef;                  // current: ce * dt / (eps0 s), E/s -= coef * J
     double beta, gam;             // voltage: E' = (E_plain - beta E - gam Vs) / (1 + beta) (gam includes 1/s)
@@ -95,7 +97,7 @@ struct Source {
 struct Probe {
     long long node;
     int comp;
-    int pad;
+    int i, j, k;                  // the node
 };
 
 // Everything a kernel needs about one board; lives in device memory.
@@ -106,7 +108,9 @@ struct Board {
     long long nodes;              // plane * (nz + 1)
     int prec;
     int pad0;
-    void *f[2][6];                // [parity][Ex, Ey, Ez, Hx, Hy, Hz]
+    void *f[3][6];                // [set][Ex, Ey, Ez, Hx, Hy, Hz]; set 2 only with two-step passes
+    int tdepth;                   // steps per interior pass: 1, or 2 (time blocking, see set_of)
+    int pair_ok;                  // the two-step pass can run on this board (set 2 and its maps exist)
     const void *cid;              // combo id per node (uint8, or uint16 if id16)
     int id16;
     int pad2;
@@ -129,6 +133,13 @@ struct Board {
     const CUtensorMap *tm;        // kNumMaps TMA descriptors (see tm_* below)
     int n_slab;
     int slab_blocks;              // slab-kernel blocks for this board
+    // Band boxes (slab[n_slab], ...): the one-node outer layer of the interior
+    // region I = [ix0,ix1) x [iy0,iy1) x [iz0,iz1) whose second step a
+    // two-step pass cannot finish.  The first n_band_h boxes (the high x and y
+    // layers) need H and E, the rest E only; their blocks follow the slab
+    // blocks, H+E boxes first.
+    int n_band, n_band_h;
+    int band_blocks, band_h_blocks;
     Slab slab[kMaxSlab];
     long long *step;              // completed steps (device counter)
     long long *stop;              // inactive once *step >= *stop
@@ -159,6 +170,16 @@ struct SlabBlock {
     int t0;                         // first slab-local thread of the block
 };
 
+// Field set that holds the state after n steps (E^n and H~^{n-1/2}).  With
+// depth 1 the sets alternate.  With depth 2 the states after an even number
+// of steps alternate between sets 0 and 1 and odd states use set 2, so one
+// pass can read the state n (even) and write the state n + 2 into the other
+// of sets 0 and 1 while the slab kernels keep the state n + 1 in set 2.
+__host__ __device__ inline int set_of(int depth, long long n)
+{
+    return depth == 2 ? ((n & 1) ? 2 : (int)((n >> 1) & 1)) : (int)(n & 1);
+}
+
 // A launch plan over one or more boards: per-phase work-item prefix sums.
 struct Plan {
     int nb;
@@ -170,17 +191,32 @@ struct Plan {
     const SlabBlock *slab_blk;    // [n_slab] per-block descriptors
     const long long *dft_prefix;  // [nb + 1] DFT warps
     long long n_int, n_zp, n_slab, n_dft;
-    int *work;                    // fused-kernel work counters [interior, z-UPML] (zeroed before every launch)
+    int *work;                    // fused-kernel work counters [interior, z-UPML, two-step] (zeroed before every launch)
     int slots;                    // resident blocks of the fused launch (set by its launcher; orders the items)
+    // two-step passes (single-board plans of a depth-2 board)
+    long long n_pair;             // two-step items (60 x 8 tiles x z segments of pair_zseg planes)
+    int pair_zseg;
+    int first_of_pair;            // k_post: the step is the first of a two-step pass (its sources
+                                  // inside I were applied by the pass)
+    long long n_band_h, n_band;   // band blocks just before slab_blk[0] (E-only first, then H+E; second step of a pair)
 };
 
 // TMA descriptor slots of a board (3D maps: x, y, plane).
-__host__ __device__ constexpr int tm_e(int par, int c) { return par * 3 + c; }               // E   box_e  x (TY+2)
-__host__ __device__ constexpr int tm_h(int par, int c) { return 6 + par * 3 + c; }           // H   box_h  x (TY+1)
-constexpr int kTmCid = 12;                                                // ids box_c* x TY
-__host__ __device__ constexpr int tm_zd(int box) { return 13 + box; }                         // D~z box_a  x TY
-__host__ __device__ constexpr int tm_zb(int box, int par) { return 15 + box * 2 + par; }        // B~z box_a  x (TY+1)
-constexpr int kNumMaps = 19;
+__host__ __device__ constexpr int tm_e(int set, int c) { return set * 3 + c; }               // E   box_e  x (TY+2)
+__host__ __device__ constexpr int tm_h(int set, int c) { return 9 + set * 3 + c; }           // H   box_h  x (TY+1)
+constexpr int kTmCid = 18;                                                // ids box_c* x TY
+__host__ __device__ constexpr int tm_zd(int box) { return 19 + box; }                         // D~z box_a  x TY
+__host__ __device__ constexpr int tm_zb(int box, int par) { return 21 + box * 2 + par; }        // B~z box_a  x (TY+1)
+// two-step pass (60 x 8 tiles): E^n and H~^{n-1/2} of sets 0/1 with two halo
+// rows below and two (E) or one (H~) above, E^{n+1} of set 2 and the ids with
+// one halo row each side
+__host__ __device__ constexpr int tp_e(int set, int c) { return 25 + set * 3 + c; }          // E   kPairEW x (8+4)
+__host__ __device__ constexpr int tp_h(int set, int c) { return 31 + set * 3 + c; }          // H   kPairEW x (8+3)
+__host__ __device__ constexpr int tp_t(int c) { return 37 + c; }                             // E   kPairEW x (8+2), set 2
+constexpr int kTpCid = 40;                                                // ids kPairC*W x (8+2)
+constexpr int kNumMaps = 41;
+constexpr int kPairCols = 60, kPairRows = 8;
+constexpr int kPairEW = 72, kPairC8W = 80, kPairC16W = 72;
 // TMA box widths for a tile of tx columns (x rounded down to 16 bytes)
 __host__ __device__ constexpr int box_up(int x, int m) { return (x + m - 1) / m * m; }
 __host__ __device__ constexpr int box_e(int tx) { return box_up(tx + 9, 8); }
@@ -209,6 +245,12 @@ enum Phase : int { kPhaseSlabH = 0, kPhaseFusedZ = 1, kPhaseInterior = 2, kPhase
 // Launchers (fdtd_kernels.cu).  All enqueue on `st`.
 cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cudaStream_t st);
 cudaError_t launch_step(const Plan &plan, int prec, int grid_cap, cudaStream_t st);
+// A pair of steps with the two-step pass (depth-2 board, even step); or one of its nine launches.
+constexpr int kPairLaunches = 9;
+constexpr int kPairPhase[kPairLaunches] = {kPhaseSlabH, kPhaseFusedZ, kPhaseInterior, kPhaseSlabE, kPhasePost,
+                                           kPhaseSlabH, kPhaseFusedZ, kPhaseSlabE,    kPhasePost};
+cudaError_t launch_pair(const Plan &plan, int prec, int grid_cap, cudaStream_t st);
+cudaError_t launch_pair_part(const Plan &plan, int prec, int idx, int grid_cap, cudaStream_t st);
 cudaError_t launch_dft(const Plan &plan, int grid_cap, cudaStream_t st);
 cudaError_t launch_set_i64(long long *p, long long v, cudaStream_t st);
 cudaError_t launch_energy(const Board *b_dev, const Board &b_host, double *partials, int n_part,

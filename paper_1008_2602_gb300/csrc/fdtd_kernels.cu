@@ -70,6 +70,32 @@ __device__ __forceinline__ bool board_active(const Board *B)
 __device__ __forceinline__ long long step_ro(const Board *B) { return __ldg(B->step); }
 __device__ __forceinline__ bool active_ro(const Board *B) { return __ldg(B->step) < __ldg(B->stop); }
 
+// Eq. 8 pulse of a source at the half step n + 1/2: J for a current source,
+// Vs for a voltage source.
+__device__ __forceinline__ double src_pulse(const Source &S, long long step, double dt)
+{
+    const double t = ((double)step + 0.5) * dt;
+    const double u = (t - S.t0) / S.tau;
+    return S.J0 * u * exp(-u * u);
+}
+
+// A source applied to the plainly updated edge value ep (as stored), given the
+// edge's previous value en (as stored); returns the new value before storage
+// rounding.  Current source: E -= coef J.  Resistive voltage source: the lumped
+// current (l E^{n+1/2} + Vs) / Rs in Ampere's law turns the plain update
+// E_p = E^n + ce S curl into E^{n+1} = (E_p - beta E^n - gam Vs) / (1 + beta).
+__device__ __forceinline__ float src_apply(const Source &S, double w, float ep, float en)
+{
+    if (S.kind == kSrcCurrent) return __fsub_rn(ep, (float)(S.coef * w));
+    return (float)(((double)ep - S.beta * (double)en - S.gam * w) / (1.0 + S.beta));
+}
+
+// Whether node (i, j, k) lies in the interior region I = [ix0,ix1) x [iy0,iy1) x [iz0,iz1).
+__device__ __forceinline__ bool in_interior(const Board *B, int i, int j, int k)
+{
+    return i >= B->ix0 && i < B->ix1 && j >= B->iy0 && j < B->iy1 && k >= B->iz0 && k < B->iz1;
+}
+
 // ------------------------------------------------------------------ fused region
 // H~^{n+1/2} components at node q straight from global memory (input parity);
 // used once per z-segment for the plane below the segment.
@@ -80,13 +106,6 @@ struct Fields {
     T *__restrict__ oex, *__restrict__ oey, *__restrict__ oez;
     T *__restrict__ ohx, *__restrict__ ohy, *__restrict__ ohz;
     Fields() = default;
-    __device__ __forceinline__ Fields(const Board *B, int par)
-    {
-        ex = (const T *)B->f[par][0]; ey = (const T *)B->f[par][1]; ez = (const T *)B->f[par][2];
-        hx = (const T *)B->f[par][3]; hy = (const T *)B->f[par][4]; hz = (const T *)B->f[par][5];
-        oex = (T *)B->f[par ^ 1][0]; oey = (T *)B->f[par ^ 1][1]; oez = (T *)B->f[par ^ 1][2];
-        ohx = (T *)B->f[par ^ 1][3]; ohy = (T *)B->f[par ^ 1][4]; ohz = (T *)B->f[par ^ 1][5];
-    }
 };
 
 __device__ __forceinline__ int cid_at(const Board *B, long long idx)
@@ -325,7 +344,8 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *b)
 struct Tile {
     const Board *B;
     int ok;
-    int i0, j0, kb, ke, kstart, par;
+    int i0, j0, kb, ke, kstart, par;   // par: step parity (B~z ping-pong)
+    int in, out;                        // field sets read and written
 };
 
 // Items of one board: x tiles fastest, then y tiles within a band of rows,
@@ -355,6 +375,9 @@ __device__ __forceinline__ Tile decode_tile(const Plan &plan, long long item)
     t.ok = active_ro(t.B) && t.B->tm_tx == kWarpCols * W && t.B->tm_ty == TY;
     const long long step = step_ro(t.B);
     t.par = (int)(step & 1);
+    const int depth = t.B->tdepth;
+    t.in = set_of(depth, step);
+    t.out = set_of(depth, step + 1);
     const long long local = item - __ldg(prefix + b);
     constexpr int TX = kWarpCols * W;
     const int ntx = (t.B->ix1 - t.B->ix0 + TX - 1) / TX, nty = (t.B->iy1 - t.B->iy0 + TY - 1) / TY;
@@ -482,10 +505,10 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
                 if (zb) bytes += St::A_BYTES;
                 mbar_expect_tx(&full[s], bytes);
                 for (int c = 0; c < 3; ++c)
-                    tma_load_3d(st + St::E_OFF + c * St::E_CS * St::ES, tm + tm_e(t.par, c), xe0, t.j0 - 1, p, &full[s]);
+                    tma_load_3d(st + St::E_OFF + c * St::E_CS * St::ES, tm + tm_e(t.in, c), xe0, t.j0 - 1, p, &full[s]);
                 if (!e_only) {
                     for (int c = 0; c < 3; ++c)
-                        tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tm_h(t.par, c), xe0, t.j0 - 1, p,
+                        tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tm_h(t.in, c), xe0, t.j0 - 1, p,
                                     &full[s]);
                     tma_load_3d(st + St::C_OFF, tm + kTmCid, xc0, t.j0, p, &full[s]);
                 }
@@ -519,7 +542,7 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
             continue;
         }
         const Board *__restrict__ B = t.B;
-        const int par = t.par, i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke, kstart = t.kstart;
+        const int par = t.par, i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke, kstart = t.kstart, oset = t.out;
         const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0, iz1 = B->iz1;
         const int X = B->pitch;
         const long long P = B->plane, NN = B->nodes;
@@ -542,8 +565,8 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
         const int xc0 = id16 ? (i0 & ~7) : (i0 & ~15);
         const int ida = max(ca - xc0, 0), idb = cb - xc0;  // columns in the id box (clamped into it)
         const bool row_slab = (jb - 1 < iy0);
-        // element (ca, jb-1, kstart) of component 0 in the output parity, advanced by P per plane
-        T *gp = (T *)B->f[par ^ 1][0] + ((long long)kstart * P + (long long)(jb - 1) * X + ca);
+        // element (ca, jb-1, kstart) of component 0 in the output set, advanced by P per plane
+        T *gp = (T *)B->f[oset][0] + ((long long)kstart * P + (long long)(jb - 1) * X + ca);
         const int zrow = B->zpitch;
         const long long zplane = (long long)(iy1 - iy0) * zrow;
         const long long zcol = (long long)(jb - iy0) * zrow + (ca - ix0);   // aux index of (ca, jb) in a plane
@@ -720,6 +743,603 @@ __global__ void __launch_bounds__(32 * W * R + 32, (FusedLayout<T, TY, W, NS, ZP
     }
 }
 
+// ------------------------------------------------------------------ two-step pass
+// Time blocking of the interior region I = [ix0,ix1) x [iy0,iy1) x [iz0,iz1)
+// (Model section: the leapfrog H^{n+1/2} from E^n, E^{n+1} from H^{n+1/2};
+// two of its steps per sweep over I).  With field sets A = set_of(2, n)
+// (n even), M = 2 and A' = set_of(2, n + 2), a pair of steps runs:
+//   k_slab_h, z-UPML launch      step n:   A -> M
+//   k_pair                       steps n, n+1 of I from A (and M, below):
+//                                  state n+2 of I minus its one-node outer
+//                                  layer (the band) -> A'; the state n+1 of
+//                                  the band and of probe and source edges -> M
+//   k_slab_e, k_post             step n:   A, M -> M (k_post skips the
+//                                  sources inside I, which the pass applied)
+//   k_slab_h + band H boxes, z-UPML launch   step n+1: M -> A'
+//   k_slab_e + band E boxes, k_post          step n+1: M, A' -> A'
+// The pass reads from M only what the step-n launches before it wrote:
+// H~^{n+1/2} of slab nodes next to I, of the z-UPML plane below I, and
+// E^{n+1} of the z-UPML plane above I.  Values of the band that need the
+// slab kernels' state n+1 (E^{n+2} on all six faces of I but the top, H~^{n+3/2}
+// on its high x and y faces) are left to the band boxes.
+//
+// A work item is a tile of kPairCols x kPairRows owned nodes and a z segment
+// [kb, ke).  A block has a producer warp streaming planes into a ring of
+// input stages (E^n with two halo rows below and above, H~^{n-1/2} with two
+// below and one above, ids), five step-1 warps and four step-2 warps.  Lane l
+// holds the column pair g + 2l, g + 2l + 1 with g = i0 - 2 (i0 even).  Step-1
+// warp w forms H~^{n+1/2} and E^{n+1} on grid rows j0-1+2w, j0+2w (and H~ on
+// the row above) of plane k into a ring of shared-memory slots, with every
+// value rounded to the storage type, so the slots hold what a one-step
+// launch would have stored.  Step-2 warp v forms H~^{n+3/2} and E^{n+2} on
+// rows j0+2v, j0+2v+1 of plane k-1 from the slots of planes k-1 and k.  The
+// arithmetic is the one-step kernel's, element by element, so with FP32
+// storage both depths give the same bits.  (With 16-bit storage the band's
+// E, which the slab kernels finish, is formed from the stored H~ where the
+// one-step kernel uses the unrounded value.)
+template <typename T>
+struct PairStage {   // one input plane
+    static constexpr int al(int x) { return (x + 127) & ~127; }
+    static constexpr int TY = kPairRows, ES = (int)sizeof(T), EW = kPairEW;
+    static constexpr int E_COMP = (TY + 4) * EW, H_COMP = (TY + 3) * EW, M_COMP = (TY + 2) * EW;
+    static constexpr int E_CS = al(E_COMP * ES) / ES, H_CS = al(H_COMP * ES) / ES;
+    static constexpr int E_BYTES = 3 * E_COMP * ES, H_BYTES = 3 * H_COMP * ES, M_BYTES = 3 * M_COMP * ES;
+    static constexpr int C8_BYTES = (TY + 2) * kPairC8W, C16_BYTES = (TY + 2) * kPairC16W * 2;
+    static constexpr int E_OFF = 0, H_OFF = 3 * E_CS * ES, C_OFF = H_OFF + 3 * H_CS * ES;
+    static constexpr int ITEM_OFF = (C_OFF + (C8_BYTES > C16_BYTES ? C8_BYTES : C16_BYTES) + 7) & ~7;
+    static constexpr int BYTES = al(ITEM_OFF + 8);
+    static_assert(M_COMP <= H_CS, "the E^{n+1} box of the plane above I fits the H~ area");
+};
+template <typename T>
+struct PairSlot {    // the step-1 results of one plane: E^{n+1}, H~^{n+1/2} on rows j0-1 .. j0+8, ids of rows j0 .. j0+7
+    static constexpr int al(int x) { return (x + 127) & ~127; }
+    static constexpr int TY = kPairRows, ES = (int)sizeof(T), OW = 64;
+    static constexpr int COMP = (TY + 2) * OW;
+    static constexpr int CS = al(COMP * ES) / ES;
+    static constexpr int E_OFF = 0, H_OFF = 3 * CS * ES, ID_OFF = 6 * CS * ES;
+    static constexpr int ITEM_OFF = ID_OFF + TY * OW * 2;
+    static constexpr int BYTES = al(ITEM_OFF + 8);
+};
+constexpr int kPairW1 = 5, kPairW2 = 4;   // step-1, step-2 warps; one producer warp follows
+template <typename T>
+struct PairLayout {
+    static constexpr int NS = 3, NO = 3;
+    static constexpr int SLOT_OFF = NS * PairStage<T>::BYTES;
+    static constexpr int BAR_OFF = SLOT_OFF + NO * PairSlot<T>::BYTES;
+    static constexpr int BYTES = BAR_OFF + 2 * (NS + NO) * 8 + 16;
+    static constexpr int THREADS = 32 * (kPairW1 + kPairW2 + 1);
+    static_assert(2 * (BYTES + 1024) <= 232448, "two blocks per SM");
+};
+
+template <typename T>
+__device__ __forceinline__ float rnd(float v);
+template <>
+__device__ __forceinline__ float rnd<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float rnd<__half>(float v) { return __half2float(__float2half_rn(v)); }
+template <typename T>
+__device__ __forceinline__ float2 rnd2(float2 v) { return make_float2(rnd<T>(v.x), rnd<T>(v.y)); }
+
+struct PairTile {
+    const Board *B;
+    bool ok, bot, top;
+    int i0, j0, kb, ke;
+    int in, out;
+    long long step;
+};
+
+// Items: x tiles fastest, then tile rows within a band of about one wave,
+// then z segments, then bands (as the one-step interior launch).
+__device__ __forceinline__ PairTile decode_pair(const Plan &plan, long long item)
+{
+    PairTile t;
+    const Board *B = plan.boards[0];
+    t.B = B;
+    t.step = step_ro(B);
+    t.ok = active_ro(B) && B->pair_ok && B->tdepth == 2 && !(t.step & 1);
+    t.in = set_of(2, t.step);
+    t.out = set_of(2, t.step + 2);
+    const int ntx = (B->ix1 - B->ix0 + kPairCols - 1) / kPairCols;
+    const int nty = (B->iy1 - B->iy0 + kPairRows - 1) / kPairRows;
+    const int zs = plan.pair_zseg, iz0 = B->iz0, iz1 = B->iz1;
+    const int nseg = (iz1 - iz0 + zs - 1) / zs;
+    const int wave_rows = max(1, plan.slots / ntx), nband = (nty + wave_rows - 1) / wave_rows;
+    const int band = (nty + nband - 1) / nband;
+    const long long per_band = (long long)ntx * band * nseg;
+    const int bi = (int)(item / per_band);
+    const long long within = item - bi * per_band;
+    const int rows = min(band, nty - bi * band);
+    const long long layer = (long long)ntx * rows;
+    const int tz = (int)(within / layer);
+    const int rem = (int)(within - tz * layer);
+    t.i0 = B->ix0 + (rem % ntx) * kPairCols;
+    t.j0 = B->iy0 + (bi * band + rem / ntx) * kPairRows;
+    t.kb = iz0 + tz * zs;
+    t.ke = min(t.kb + zs, iz1);
+    t.bot = t.kb == iz0;
+    t.top = t.ke == iz1;
+    return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PairLayout<T>::THREADS, 2) k_pair(Plan plan)
+{
+    using St = PairStage<T>;
+    using Sl = PairSlot<T>;
+    using L = PairLayout<T>;
+    constexpr int NS = L::NS, NO = L::NO, TY = kPairRows, EW = St::EW, OW = Sl::OW;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + L::BAR_OFF);
+    uint64_t *empty = full + NS;
+    uint64_t *ofull = empty + NS;
+    uint64_t *oempty = ofull + NO;
+    int *abort_flag = reinterpret_cast<int *>(oempty + NO);
+    const int lx = threadIdx.x, wy = threadIdx.y;
+    int *const status0 = plan.boards[0]->status;
+
+    if (wy == 0 && lx == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kPairW1);
+        }
+        for (int o = 0; o < NO; ++o) {
+            mbar_init(&ofull[o], kPairW1);
+            mbar_init(&oempty[o], kPairW2);
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (wy == kPairW1 + kPairW2) {
+        // ------------------------------------------------------------ producer
+        // planes ps .. pe of an item: ps = kb - 2 (kb at the bottom of I), pe =
+        // ke + 1 (E^n only), or at the top of I pe = ke = iz1 with E^n and
+        // the E^{n+1} that the z-UPML launch of step n wrote into M
+        if (lx != 0) return;
+        uint32_t eph = 0;
+        long long q = 0;
+        int s = 0;
+        auto acquire = [&]() {
+            if (q >= NS) {
+                mbar_wait(&empty[s], (eph >> s) & 1u, status0, abort_flag);
+                eph ^= 1u << s;
+            }
+        };
+        for (;;) {
+            const long long item = atomicAdd(plan.work + 2, 1);
+            if (item >= plan.n_pair) break;
+            const PairTile t = decode_pair(plan, item);
+            if (!t.ok) continue;   // nothing is sent for an item that does not run
+            const Board *B = t.B;
+            const CUtensorMap *tm = B->tm;
+            const int id16 = B->id16;
+            const int g = t.i0 - 2;
+            const int xe0 = g & ~(16 / St::ES - 1);
+            const int xc0 = id16 ? (g & ~7) : (g & ~15);
+            const int ps = t.bot ? t.kb : t.kb - 2, pe = t.top ? t.ke : t.ke + 1;
+            for (int p = ps; p <= pe; ++p, ++q, s = (s + 1 == NS ? 0 : s + 1)) {
+                acquire();
+                unsigned char *st = smem + s * St::BYTES;
+                *reinterpret_cast<volatile long long *>(st + St::ITEM_OFF) = (p == ps) ? item : -2;
+                const bool last = p == pe;
+                uint32_t bytes = St::E_BYTES;
+                if (last && t.top) bytes += St::M_BYTES;
+                else if (!last) bytes += St::H_BYTES + (id16 ? St::C16_BYTES : St::C8_BYTES);
+                mbar_expect_tx(&full[s], bytes);
+                for (int c = 0; c < 3; ++c)
+                    tma_load_3d(st + St::E_OFF + c * St::E_CS * St::ES, tm + tp_e(t.in, c), xe0, t.j0 - 2, p, &full[s]);
+                if (last && t.top) {
+                    for (int c = 0; c < 3; ++c)
+                        tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tp_t(c), xe0, t.j0 - 1, p, &full[s]);
+                } else if (!last) {
+                    for (int c = 0; c < 3; ++c)
+                        tma_load_3d(st + St::H_OFF + c * St::H_CS * St::ES, tm + tp_h(t.in, c), xe0, t.j0 - 2, p,
+                                    &full[s]);
+                    tma_load_3d(st + St::C_OFF, tm + kTpCid, xc0, t.j0 - 1, p, &full[s]);
+                }
+            }
+        }
+        acquire();
+        *reinterpret_cast<volatile long long *>(smem + s * St::BYTES + St::ITEM_OFF) = -1;
+        mbar_expect_tx(&full[s], 0);
+        return;
+    }
+
+    const bool step1 = wy < kPairW1;
+    const int w = step1 ? wy : wy - kPairW1;
+    if (step1) {
+        // ------------------------------------------------------------ step 1
+        uint32_t fph = 0, oeph = 0;
+        int sq = 0, so = 0;
+        long long nslot = 0;
+        auto slot_acquire = [&]() {
+            if (nslot >= NO) {
+                mbar_wait(&oempty[so], (oeph >> so) & 1u, status0, abort_flag);
+                oeph ^= 1u << so;
+            }
+        };
+        auto slot_publish = [&]() {
+            __syncwarp();
+            if (lx == 0) mbar_arrive(&ofull[so]);
+            so = so + 1 == NO ? 0 : so + 1;
+            ++nslot;
+        };
+        for (;;) {
+            mbar_wait(&full[sq], (fph >> sq) & 1u, status0, abort_flag);
+            const long long item = *reinterpret_cast<volatile long long *>(smem + sq * St::BYTES + St::ITEM_OFF);
+            if (item < 0) {   // no more work: pass the end mark to the step-2 warps
+                slot_acquire();
+                if (w == 0 && lx == 0)
+                    *reinterpret_cast<volatile long long *>(smem + L::SLOT_OFF + so * Sl::BYTES + Sl::ITEM_OFF) = -1;
+                slot_publish();
+                break;
+            }
+            fph ^= 1u << sq;
+            const PairTile t = decode_pair(plan, item);
+            const Board *__restrict__ B = t.B;
+            const int i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke;
+            const bool top = t.top;
+            const int ps = t.bot ? kb : kb - 2, q0 = t.bot ? kb : kb - 1;
+            const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0, iz1 = B->iz1;
+            const int X = B->pitch, ny = B->ny;
+            const long long P = B->plane, NN = B->nodes;
+            const float2 Sx2 = make_float2(B->S[0], B->S[0]), Sy2 = make_float2(B->S[1], B->S[1]);
+            const float2 Sz2 = make_float2(B->S[2], B->S[2]);
+            const float2 nSx2 = make_float2(-B->S[0], -B->S[0]), nSy2 = make_float2(-B->S[1], -B->S[1]);
+            const float2 nSz2 = make_float2(-B->S[2], -B->S[2]);
+            const int id16 = B->id16;
+            const float4 *__restrict__ ctab = B->ctab;
+            int *const status = B->status;
+            T *const Mp = (T *)B->f[2][0];
+            const int g = i0 - 2;
+            const int ca = g + 2 * lx, cb = ca + 1;
+            const int whi = min(i0 + kPairCols, ix1);
+            const bool own_a = ca >= i0 && ca < whi, own_b = cb >= i0 && cb < whi;
+            const bool slab_a = ca < ix0 && ca >= 0, slab_b = cb < ix0 && cb >= 0;
+            const int ecol = (g - (g & ~(16 / St::ES - 1))) + 2 * lx;
+            const int xc0 = id16 ? (g & ~7) : (g & ~15);
+            const int ida = ca - xc0, idb = ida + 1;
+            const int jr = j0 - 1 + 2 * w;     // first row of this warp
+            // sources in the step-1 region, probes on owned nodes (rare: checked per item)
+            bool src_here = false, probe_here = false;
+            for (int s = 0; s < B->n_src; ++s) {
+                const Source &S = B->src[s];
+                src_here |= S.i >= g && S.i < g + 64 && S.j >= jr && S.j < jr + 2 && S.k >= q0 && S.k <= ke;
+            }
+            for (int s = 0; s < B->n_probe; ++s) {
+                const Probe &Q = B->probe[s];
+                probe_here |= Q.i >= i0 && Q.i < whi && Q.j >= jr && Q.j < jr + 2 && Q.k >= kb && Q.k < ke;
+            }
+            const double dt = B->dt;
+            const long long step = t.step;
+
+            float2 hk1x[2], hk1y[2];   // H~^{n+1/2} x, y of the previous plane
+#pragma unroll
+            for (int r = 0; r < 2; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
+            if (t.bot) {   // plane iz0 - 1 (z-UPML or slab) was written by the launches of step n
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const int j = jr + r;
+                    if (j < 0 || j > ny) continue;
+                    const T *gq = Mp + (long long)(iz0 - 1) * P + (long long)j * X;
+                    if (ca >= 0 && ca < X) { hk1x[r].x = Io<T>::ld(gq + 3 * NN + ca); hk1y[r].x = Io<T>::ld(gq + 4 * NN + ca); }
+                    if (cb >= 0 && cb < X) { hk1x[r].y = Io<T>::ld(gq + 3 * NN + cb); hk1y[r].y = Io<T>::ld(gq + 4 * NN + cb); }
+                }
+            }
+            int s0 = sq;
+            for (int k = ps;; ++k) {
+                const bool pseudo = top && k == ke;
+                const int s1 = s0 + 1 == NS ? 0 : s0 + 1;
+                if (!pseudo) {
+                    mbar_wait(&full[s1], (fph >> s1) & 1u, status, abort_flag);
+                    fph ^= 1u << s1;
+                }
+                const bool wslot = k >= q0;
+                unsigned char *sl = smem + L::SLOT_OFF + so * Sl::BYTES;
+                if (wslot) {
+                    slot_acquire();
+                    if (k == q0 && w == 0 && lx == 0) *reinterpret_cast<volatile long long *>(sl + Sl::ITEM_OFF) = item;
+                }
+                const unsigned char *st0 = smem + s0 * St::BYTES, *st1 = smem + s1 * St::BYTES;
+                if (pseudo) {
+                    // plane iz1: E^{n+1} as the z-UPML launch of step n stored it (box rows from j0 - 1)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const T *mt = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol + (2 * w + r) * EW;
+                        T *se = reinterpret_cast<T *>(sl + Sl::E_OFF) + (2 * w + r) * OW + 2 * lx;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) Pair<T>::st(se + c * Sl::CS, Pair<T>::lds(mt + c * St::H_CS));
+                    }
+                } else {
+                    // box rows from 2w: the row above the warp's rows (E and H~ boxes start at j0 - 2)
+                    const T *E0 = reinterpret_cast<const T *>(st0 + St::E_OFF) + ecol + 2 * w * EW;
+                    const T *E1 = reinterpret_cast<const T *>(st1 + St::E_OFF) + ecol + 2 * w * EW;
+                    const T *H0 = reinterpret_cast<const T *>(st0 + St::H_OFF) + ecol + 2 * w * EW;
+                    const unsigned char *C0 = st0 + St::C_OFF + 2 * w * (id16 ? 2 * kPairC16W : kPairC8W);
+                    constexpr int ECS = St::E_CS, HCS = St::H_CS;
+                    const bool full_plane = k >= q0;
+                    float4 cea[2], ceb[2];
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int ia = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * kPairC16W + ida]
+                                            : (int)C0[r * kPairC8W + ida];
+                        const int ib = id16 ? (int)reinterpret_cast<const uint16_t *>(C0)[r * kPairC16W + idb]
+                                            : (int)C0[r * kPairC8W + idb];
+                        cea[r] = __ldg(ctab + ia);
+                        ceb[r] = __ldg(ctab + ib);
+                        // the ids of the step-2 rows (slot id rows start at j0)
+                        const int idr = 2 * w - 1 + r;
+                        if (full_plane && idr >= 0 && idr < TY) {
+                            if (id16)
+                                *reinterpret_cast<uint32_t *>(sl + Sl::ID_OFF + (idr * OW + 2 * lx) * 2) =
+                                    (uint32_t)ia | ((uint32_t)ib << 16);
+                            else
+                                *reinterpret_cast<uint16_t *>(sl + Sl::ID_OFF + idr * OW + 2 * lx) =
+                                    (uint16_t)(ia | (ib << 8));
+                        }
+                    }
+                    auto hrow = [&](int rr, float2 &ex, float2 &ey, float2 &ez, float2 &hx, float2 &hy, float2 &hz) {
+                        ez = Pair<T>::lds(E0 + 2 * ECS + rr * EW);
+                        ey = Pair<T>::lds(E0 + ECS + rr * EW);
+                        ex = Pair<T>::lds(E0 + rr * EW);
+                        const float2 ezu = Pair<T>::lds(E0 + 2 * ECS + (rr + 1) * EW);
+                        const float2 exu = Pair<T>::lds(E0 + (rr + 1) * EW);
+                        const float2 eyk = Pair<T>::lds(E1 + ECS + rr * EW), exk = Pair<T>::lds(E1 + rr * EW);
+                        const float ez2 = cvt<T>(E0[2 * ECS + rr * EW + 2]), ey2 = cvt<T>(E0[ECS + rr * EW + 2]);
+                        const float2 ezx = make_float2(ez.y, ez2), eyx = make_float2(ey.y, ey2);
+                        const float2 scx = curl2v(ezu, ez, eyk, ey, Sy2, nSz2);
+                        const float2 scy = curl2v(exk, ex, ezx, ez, Sz2, nSx2);
+                        const float2 scz = curl2v(eyx, ey, exu, ex, Sx2, nSy2);
+                        hx = sub2(Pair<T>::lds(H0 + rr * EW), scx);
+                        hy = sub2(Pair<T>::lds(H0 + HCS + rr * EW), scy);
+                        hz = sub2(Pair<T>::lds(H0 + 2 * HCS + rr * EW), scz);
+                    };
+                    // H~ outside the fused region (low x columns, low y rows) comes from the slab output in M
+                    auto slab_fix = [&](int j, float2 &hx, float2 &hy, float2 &hz) {
+                        if (j < 0 || j >= iy1) return;
+                        const bool row_out = j < iy0;
+                        const bool fa = (row_out || slab_a) && ca >= 0 && ca < X;
+                        const bool fb = (row_out || slab_b) && cb >= 0 && cb < X;
+                        if (!fa && !fb) return;
+                        const T *gq = Mp + (long long)k * P + (long long)j * X;
+                        if (fa) { hx.x = Io<T>::ld(gq + 3 * NN + ca); hy.x = Io<T>::ld(gq + 4 * NN + ca); hz.x = Io<T>::ld(gq + 5 * NN + ca); }
+                        if (fb) { hx.y = Io<T>::ld(gq + 3 * NN + cb); hy.y = Io<T>::ld(gq + 4 * NN + cb); hz.y = Io<T>::ld(gq + 5 * NN + cb); }
+                    };
+                    float2 px, pz;   // H~x, H~z at (., j-1)
+                    {
+                        float2 ex, ey, ez, hy;
+                        hrow(0, ex, ey, ez, px, hy, pz);
+                        slab_fix(jr - 1, px, hy, pz);
+                    }
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        const int j = jr + r;
+                        float2 ex, ey, ez, hx, hy, hz;
+                        hrow(r + 1, ex, ey, ez, hx, hy, hz);
+                        slab_fix(j, hx, hy, hz);
+                        const float hyl = __shfl_up_sync(0xffffffffu, hy.y, 1);
+                        const float hzl = __shfl_up_sync(0xffffffffu, hz.y, 1);
+                        if (full_plane) {
+                            const float2 hym = make_float2(hyl, hy.x), hzm = make_float2(hzl, hz.x);
+                            const float2 scx = curl2v(hz, pz, hy, hk1y[r], Sy2, nSz2);
+                            const float2 scy = curl2v(hx, hk1x[r], hz, hzm, Sz2, nSx2);
+                            const float2 scz = curl2v(hy, hym, hx, px, Sx2, nSy2);
+                            float2 exv = rnd2<T>(make_float2(__fmaf_rn(cea[r].x, scx.x, ex.x), __fmaf_rn(ceb[r].x, scx.y, ex.y)));
+                            float2 eyv = rnd2<T>(make_float2(__fmaf_rn(cea[r].y, scy.x, ey.x), __fmaf_rn(ceb[r].y, scy.y, ey.y)));
+                            float2 ezv = rnd2<T>(make_float2(__fmaf_rn(cea[r].z, scz.x, ez.x), __fmaf_rn(ceb[r].z, scz.y, ez.y)));
+                            if (src_here) {   // Eq. 8 sources of step n on this row, in the order k_post applies them
+                                for (int s = 0; s < B->n_src; ++s) {
+                                    const Source &S = B->src[s];
+                                    if (S.k != k || S.j != j || (S.i != ca && S.i != cb)) continue;
+                                    const double wv = src_pulse(S, step, dt);
+                                    float2 e = S.comp == 0 ? exv : (S.comp == 1 ? eyv : ezv);
+                                    const float2 en = S.comp == 0 ? ex : (S.comp == 1 ? ey : ez);
+                                    if (S.i == ca) e.x = rnd<T>(src_apply(S, wv, e.x, en.x));
+                                    else e.y = rnd<T>(src_apply(S, wv, e.y, en.y));
+                                    if (S.comp == 0) exv = e;
+                                    else if (S.comp == 1) eyv = e;
+                                    else ezv = e;
+                                }
+                            }
+                            T *se = reinterpret_cast<T *>(sl + Sl::E_OFF) + (2 * w + r) * OW + 2 * lx;
+                            Pair<T>::st(se, exv);
+                            Pair<T>::st(se + Sl::CS, eyv);
+                            Pair<T>::st(se + 2 * Sl::CS, ezv);
+                            T *sh = reinterpret_cast<T *>(sl + Sl::H_OFF) + (2 * w + r) * OW + 2 * lx;
+                            Pair<T>::st(sh, hx);
+                            Pair<T>::st(sh + Sl::CS, hy);
+                            Pair<T>::st(sh + 2 * Sl::CS, hz);
+                            // the state n+1 of owned band nodes (and of probe and source edges) goes to M
+                            if (k >= kb && k < ke && j >= j0 && j < j0 + TY && j < iy1) {
+                                const bool ze = k == iz0 || k == iz1 - 1, zh = k == iz1 - 1;
+                                const bool ye = j == iy0 || j == iy1 - 1, yh = j == iy1 - 1;
+                                bool wea = own_a && (ze || ye || ca == ix0 || ca == ix1 - 1);
+                                bool web = own_b && (ze || ye || cb == ix0 || cb == ix1 - 1);
+                                const bool wha = own_a && (zh || yh || ca == ix1 - 1);
+                                const bool whb = own_b && (zh || yh || cb == ix1 - 1);
+                                if (probe_here)
+                                    for (int s = 0; s < B->n_probe; ++s) {
+                                        const Probe &Q = B->probe[s];
+                                        if (Q.k == k && Q.j == j) { wea |= own_a && Q.i == ca; web |= own_b && Q.i == cb; }
+                                    }
+                                if (src_here)
+                                    for (int s = 0; s < B->n_src; ++s) {
+                                        const Source &S = B->src[s];
+                                        if (S.k == k && S.j == j) { wea |= own_a && S.i == ca; web |= own_b && S.i == cb; }
+                                    }
+                                T *o = Mp + (long long)k * P + (long long)j * X + ca;
+                                if (wea && web) {
+                                    stg2(o, exv); stg2(o + NN, eyv); stg2(o + 2 * NN, ezv);
+                                } else if (wea) {
+                                    stg1(o, exv.x); stg1(o + NN, eyv.x); stg1(o + 2 * NN, ezv.x);
+                                } else if (web) {
+                                    stg1(o + 1, exv.y); stg1(o + NN + 1, eyv.y); stg1(o + 2 * NN + 1, ezv.y);
+                                }
+                                if (wha && whb) {
+                                    stg2(o + 3 * NN, hx); stg2(o + 4 * NN, hy); stg2(o + 5 * NN, hz);
+                                } else if (wha) {
+                                    stg1(o + 3 * NN, hx.x); stg1(o + 4 * NN, hy.x); stg1(o + 5 * NN, hz.x);
+                                } else if (whb) {
+                                    stg1(o + 3 * NN + 1, hx.y); stg1(o + 4 * NN + 1, hy.y); stg1(o + 5 * NN + 1, hz.y);
+                                }
+                            }
+                        }
+                        hk1x[r] = hx;
+                        hk1y[r] = hy;
+                        px = hx;
+                        pz = hz;
+                    }
+                }
+                if (wslot) slot_publish();
+                __syncwarp();
+                if (lx == 0) mbar_arrive(&empty[s0]);
+                s0 = s1;
+                if (k == ke) break;
+            }
+            if (!top) {   // the E-only plane above the segment
+                __syncwarp();
+                if (lx == 0) mbar_arrive(&empty[s0]);
+                s0 = s0 + 1 == NS ? 0 : s0 + 1;
+            }
+            sq = s0;
+        }
+        return;
+    }
+
+    // ---------------------------------------------------------------- step 2
+    uint32_t ofph = 0;
+    int so = 0;
+    for (;;) {
+        mbar_wait(&ofull[so], (ofph >> so) & 1u, status0, abort_flag);
+        const long long item = *reinterpret_cast<volatile long long *>(smem + L::SLOT_OFF + so * Sl::BYTES + Sl::ITEM_OFF);
+        if (item < 0) break;
+        ofph ^= 1u << so;
+        const PairTile t = decode_pair(plan, item);
+        const Board *__restrict__ B = t.B;
+        const int i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke;
+        const int q0 = t.bot ? kb : kb - 1;
+        const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0;
+        const int X = B->pitch;
+        const long long P = B->plane, NN = B->nodes;
+        const float2 Sx2 = make_float2(B->S[0], B->S[0]), Sy2 = make_float2(B->S[1], B->S[1]);
+        const float2 Sz2 = make_float2(B->S[2], B->S[2]);
+        const float2 nSx2 = make_float2(-B->S[0], -B->S[0]), nSy2 = make_float2(-B->S[1], -B->S[1]);
+        const float2 nSz2 = make_float2(-B->S[2], -B->S[2]);
+        const int id16 = B->id16;
+        const float4 *__restrict__ ctab = B->ctab;
+        int *const status = B->status;
+        const int g = i0 - 2;
+        const int ca = g + 2 * lx, cb = ca + 1;
+        const int whi = min(i0 + kPairCols, ix1);
+        const bool own_a = ca >= i0 && ca < whi, own_b = cb >= i0 && cb < whi;
+        // stores: H~^{n+3/2} off the high x face, E^{n+2} off both x faces (the band's)
+        const bool sha = own_a && ca != ix1 - 1, shb = own_b && cb != ix1 - 1;
+        const bool sea = sha && ca != ix0, seb = shb && cb != ix0;
+        const int jb = j0 + 2 * w;   // first row of this warp
+        T *gp = (T *)B->f[t.out][0] + ((long long)q0 * P + (long long)jb * X + ca);
+        float2 hk1x[2], hk1y[2];   // H~^{n+3/2} x, y of the previous plane
+#pragma unroll
+        for (int r = 0; r < 2; ++r) { hk1x[r] = make_float2(0.f, 0.f); hk1y[r] = make_float2(0.f, 0.f); }
+        int o0 = so;
+        for (int q = q0; q < ke; ++q, gp += P) {
+            const int o1 = o0 + 1 == NO ? 0 : o0 + 1;
+            mbar_wait(&ofull[o1], (ofph >> o1) & 1u, status, abort_flag);
+            ofph ^= 1u << o1;
+            const unsigned char *sl0 = smem + L::SLOT_OFF + o0 * Sl::BYTES, *sl1 = smem + L::SLOT_OFF + o1 * Sl::BYTES;
+            // slot rows from 2w: the row above the warp's rows (slot rows start at j0 - 1)
+            const T *E0 = reinterpret_cast<const T *>(sl0 + Sl::E_OFF) + 2 * lx + 2 * w * OW;
+            const T *E1 = reinterpret_cast<const T *>(sl1 + Sl::E_OFF) + 2 * lx + 2 * w * OW;
+            const T *H0 = reinterpret_cast<const T *>(sl0 + Sl::H_OFF) + 2 * lx + 2 * w * OW;
+            constexpr int CS = Sl::CS;
+            const bool hplane = q >= kb, eplane = q >= kb && q != iz0;
+            float4 cea[2], ceb[2];
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int row = 2 * w + r;   // id rows of the slot start at j0
+                int ia, ib;
+                if (id16) {
+                    const uint32_t v = *reinterpret_cast<const uint32_t *>(sl0 + Sl::ID_OFF + (row * OW + 2 * lx) * 2);
+                    ia = (int)(v & 0xffffu); ib = (int)(v >> 16);
+                } else {
+                    const uint32_t v = *reinterpret_cast<const uint16_t *>(sl0 + Sl::ID_OFF + row * OW + 2 * lx);
+                    ia = (int)(v & 0xffu); ib = (int)(v >> 8);
+                }
+                cea[r] = __ldg(ctab + ia);
+                ceb[r] = __ldg(ctab + ib);
+            }
+            auto hrow = [&](int rr, float2 &ex, float2 &ey, float2 &ez, float2 &hx, float2 &hy, float2 &hz) {
+                ez = Pair<T>::lds(E0 + 2 * CS + rr * OW);
+                ey = Pair<T>::lds(E0 + CS + rr * OW);
+                ex = Pair<T>::lds(E0 + rr * OW);
+                const float2 ezu = Pair<T>::lds(E0 + 2 * CS + (rr + 1) * OW);
+                const float2 exu = Pair<T>::lds(E0 + (rr + 1) * OW);
+                const float2 eyk = Pair<T>::lds(E1 + CS + rr * OW), exk = Pair<T>::lds(E1 + rr * OW);
+                const float ez2 = cvt<T>(E0[2 * CS + rr * OW + 2]), ey2 = cvt<T>(E0[CS + rr * OW + 2]);
+                const float2 ezx = make_float2(ez.y, ez2), eyx = make_float2(ey.y, ey2);
+                const float2 scx = curl2v(ezu, ez, eyk, ey, Sy2, nSz2);
+                const float2 scy = curl2v(exk, ex, ezx, ez, Sz2, nSx2);
+                const float2 scz = curl2v(eyx, ey, exu, ex, Sx2, nSy2);
+                hx = sub2(Pair<T>::lds(H0 + rr * OW), scx);
+                hy = sub2(Pair<T>::lds(H0 + CS + rr * OW), scy);
+                hz = sub2(Pair<T>::lds(H0 + 2 * CS + rr * OW), scz);
+            };
+            float2 px, pz;
+            {
+                float2 ex, ey, ez, hy;
+                hrow(0, ex, ey, ez, px, hy, pz);
+            }
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const int j = jb + r;
+                float2 ex, ey, ez, hx, hy, hz;
+                hrow(r + 1, ex, ey, ez, hx, hy, hz);
+                const float hyl = __shfl_up_sync(0xffffffffu, hy.y, 1);
+                const float hzl = __shfl_up_sync(0xffffffffu, hz.y, 1);
+                if (hplane && j < iy1) {
+                    T *o = gp + (long long)r * X;
+                    const bool yh = j != iy1 - 1, ye = yh && j != iy0;
+                    const bool ha = sha && yh, hb = shb && yh;
+                    if (ha && hb) {
+                        stg2(o + 3 * NN, hx); stg2(o + 4 * NN, hy); stg2(o + 5 * NN, hz);
+                    } else if (ha) {
+                        stg1(o + 3 * NN, hx.x); stg1(o + 4 * NN, hy.x); stg1(o + 5 * NN, hz.x);
+                    } else if (hb) {
+                        stg1(o + 3 * NN + 1, hx.y); stg1(o + 4 * NN + 1, hy.y); stg1(o + 5 * NN + 1, hz.y);
+                    }
+                    if (eplane) {
+                        const float2 hym = make_float2(hyl, hy.x), hzm = make_float2(hzl, hz.x);
+                        const float2 scx = curl2v(hz, pz, hy, hk1y[r], Sy2, nSz2);
+                        const float2 scy = curl2v(hx, hk1x[r], hz, hzm, Sz2, nSx2);
+                        const float2 scz = curl2v(hy, hym, hx, px, Sx2, nSy2);
+                        const float2 exv = make_float2(__fmaf_rn(cea[r].x, scx.x, ex.x), __fmaf_rn(ceb[r].x, scx.y, ex.y));
+                        const float2 eyv = make_float2(__fmaf_rn(cea[r].y, scy.x, ey.x), __fmaf_rn(ceb[r].y, scy.y, ey.y));
+                        const float2 ezv = make_float2(__fmaf_rn(cea[r].z, scz.x, ez.x), __fmaf_rn(ceb[r].z, scz.y, ez.y));
+                        const bool ea = sea && ye, eb = seb && ye;
+                        if (ea && eb) {
+                            stg2(o, exv); stg2(o + NN, eyv); stg2(o + 2 * NN, ezv);
+                        } else if (ea) {
+                            stg1(o, exv.x); stg1(o + NN, eyv.x); stg1(o + 2 * NN, ezv.x);
+                        } else if (eb) {
+                            stg1(o + 1, exv.y); stg1(o + NN + 1, eyv.y); stg1(o + 2 * NN + 1, ezv.y);
+                        }
+                    }
+                }
+                hk1x[r] = hx;
+                hk1y[r] = hy;
+                px = hx;
+                pz = hz;
+            }
+            __syncwarp();
+            if (lx == 0) mbar_arrive(&oempty[o0]);
+            o0 = o1;
+        }
+        __syncwarp();
+        if (lx == 0) mbar_arrive(&oempty[o0]);   // the slot of plane ke
+        so = o0 + 1 == NO ? 0 : o0 + 1;
+    }
+}
+
 // ------------------------------------------------------------------ slabs
 // A slab thread marches kSlabKz consecutive nodes of its slab: along z for
 // slabs more than one plane thick (an (i, j) column), along y for the two
@@ -735,7 +1355,7 @@ struct SlabCol {
 };
 
 // Block set-up from the plan's per-block descriptor: the step counters, the
-// slab's box and both parities' field pointers are independent loads.
+// slab's box and every set's field pointers are independent loads.
 template <typename T>
 __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, const Board *&B, SlabCol &sc,
                                             Fields<T> &F)
@@ -745,12 +1365,14 @@ __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, con
     const long long step = __ldg(d.step), stop = __ldg(d.stop);
     const Slab *sl = &B->slab[d.slab];
     const int ni = sl->ni, nj = sl->nj, i0 = sl->i0, j0 = sl->j0, k0 = sl->k0, k1 = sl->k1, j1 = sl->j1;
-    const void *f0[6], *f1[6];
+    const void *f0[6], *f1[6], *f2[6];
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         f0[c] = B->f[0][c];
         f1[c] = B->f[1][c];
+        f2[c] = B->f[2][c];
     }
+    const int depth = B->tdepth;
     if (step >= stop) return false;
     const bool ym = (k1 - k0 == 1);
     const int nij = ni * nj;
@@ -779,11 +1401,12 @@ __device__ __forceinline__ bool slab_locate(const Plan &plan, long long blk, con
     }
     sc.ym = ym;
     sc.sl = sl;
-    const bool p1 = (step & 1) != 0;
-    F.ex = (const T *)(p1 ? f1[0] : f0[0]); F.ey = (const T *)(p1 ? f1[1] : f0[1]); F.ez = (const T *)(p1 ? f1[2] : f0[2]);
-    F.hx = (const T *)(p1 ? f1[3] : f0[3]); F.hy = (const T *)(p1 ? f1[4] : f0[4]); F.hz = (const T *)(p1 ? f1[5] : f0[5]);
-    F.oex = (T *)(p1 ? f0[0] : f1[0]); F.oey = (T *)(p1 ? f0[1] : f1[1]); F.oez = (T *)(p1 ? f0[2] : f1[2]);
-    F.ohx = (T *)(p1 ? f0[3] : f1[3]); F.ohy = (T *)(p1 ? f0[4] : f1[4]); F.ohz = (T *)(p1 ? f0[5] : f1[5]);
+    const int si = set_of(depth, step), so = set_of(depth, step + 1);
+    auto pick = [&](int set, int c) -> const void * { return set == 0 ? f0[c] : (set == 1 ? f1[c] : f2[c]); };
+    F.ex = (const T *)pick(si, 0); F.ey = (const T *)pick(si, 1); F.ez = (const T *)pick(si, 2);
+    F.hx = (const T *)pick(si, 3); F.hy = (const T *)pick(si, 4); F.hz = (const T *)pick(si, 5);
+    F.oex = (T *)pick(so, 0); F.oey = (T *)pick(so, 1); F.oez = (T *)pick(so, 2);
+    F.ohx = (T *)pick(so, 3); F.ohy = (T *)pick(so, 4); F.ohz = (T *)pick(so, 5);
     return true;
 }
 
@@ -1160,38 +1783,34 @@ __global__ void k_post(Plan plan)
     const Probe *const probe = B->probe;
     const double dt = B->dt;
     const float scale = B->scale;
-    void *fp[2][3];
+    void *fp[3][3];
 #pragma unroll
-    for (int q = 0; q < 2; ++q)
+    for (int q = 0; q < 3; ++q)
 #pragma unroll
         for (int c = 0; c < 3; ++c) fp[q][c] = B->f[q][c];
+    const int depth = B->tdepth;
+    const bool skip_i = plan.first_of_pair != 0;
     Source s0;
     Probe q0;
     if (tid < n_src) s0 = src[tid];
     if (tid < n_probe) q0 = probe[tid];
     const long long step = *((volatile long long *)B->step);
     if (step >= *((volatile long long *)B->stop)) return;
-    const int out = (int)(step & 1) ^ 1;
-    auto field = [&](int par, int comp) -> T * { return (T *)(comp == 0 ? fp[par][0] : comp == 1 ? fp[par][1] : fp[par][2]); };
+    const int out = set_of(depth, step + 1), in = set_of(depth, step);
+    auto field = [&](int set, int comp) -> T * {
+        void *const *f = set == 0 ? fp[0] : (set == 1 ? fp[1] : fp[2]);
+        return (T *)(comp == 0 ? f[0] : comp == 1 ? f[1] : f[2]);
+    };
     // sources on distinct edges are independent: one thread each; sources
-    // sharing an edge are applied in order by thread 0
+    // sharing an edge are applied in order by thread 0.  On the first step of
+    // a two-step pass the pass has applied the sources inside I already.
     if (par_src || tid == 0) {
-        const double t = ((double)step + 0.5) * dt;
         for (int s = par_src ? tid : 0; s < n_src; s += par_src ? (int)blockDim.x : 1) {
             const Source S = (par_src && s == tid) ? s0 : src[s];
-            const double u = (t - S.t0) / S.tau;
-            const double w = S.J0 * u * exp(-u * u);   // Eq. 8 pulse: J, or Vs for a voltage source
+            if (skip_i && in_interior(B, S.i, S.j, S.k)) continue;
+            const double w = src_pulse(S, step, dt);
             T *e = field(out, S.comp) + S.node;
-            if (S.kind == kSrcCurrent) {
-                Io<T>::st(e, __fsub_rn(Io<T>::ldw(e), (float)(S.coef * w)));
-            } else {
-                // resistive voltage source: the lumped current (l E^{n+1/2} + Vs)/Rs
-                // in Ampere's law turns the plain update E_p = E^n + ce S curl into
-                // E^{n+1} = (E_p - beta E^n - gam Vs) / (1 + beta)
-                const double ep = Io<T>::ldw(e);
-                const double en = Io<T>::ldw((const T *)field(out ^ 1, S.comp) + S.node);
-                Io<T>::st(e, (float)((ep - S.beta * en - S.gam * w) / (1.0 + S.beta)));
-            }
+            Io<T>::st(e, src_apply(S, w, Io<T>::ldw(e), Io<T>::ldw((const T *)field(in, S.comp) + S.node)));
         }
     }
     __syncthreads();
@@ -1281,7 +1900,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_energy(const Board *B, double *partials)
 {
     const long long step = *((volatile long long *)B->step);
-    const int pin = (int)((step - 1) & 1), pout = (int)(step & 1);
+    const int pin = set_of(B->tdepth, step - 1), pout = set_of(B->tdepth, step);
     const int nx = B->nx, ny = B->ny, nz = B->nz, X = B->pitch;
     const long long P = B->plane;
     const long long total = (long long)(nx + 1) * (ny + 1) * (nz + 1);
@@ -1435,6 +2054,37 @@ static void launch_fused(const Plan &plan, cudaStream_t st)
     }
 }
 
+// Two-step pass: two blocks per SM (shared memory), one launch per pair of steps.
+template <typename T>
+struct PairCfg {
+    using L = PairLayout<T>;
+    static dim3 block() { return dim3(32, kPairW1 + kPairW2 + 1); }
+    static int grid()
+    {
+        static int g = 0;
+        if (!g) {
+            int dev = 0, sms = 0, per = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pair<T>, L::THREADS, L::BYTES);
+            g = (sms > 0 ? sms : 152) * (per > 0 ? per : 1);
+        }
+        return g;
+    }
+    static cudaError_t set_limit()
+    {
+        return cudaFuncSetAttribute(k_pair<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::BYTES);
+    }
+    static void launch(const Plan &plan, cudaStream_t st)
+    {
+        if (plan.n_pair <= 0) return;
+        const int g = (int)(plan.n_pair < grid() ? plan.n_pair : grid());
+        Plan p = plan;
+        p.slots = grid();
+        k_pair<T><<<g, block(), L::BYTES, st>>>(p);
+    }
+};
+
 // Slab kernels launch one block per descriptor (grid-striding past this).
 constexpr long long kMaxGrid = 1 << 20;
 
@@ -1477,6 +2127,51 @@ cudaError_t launch_phase(const Plan &plan, int prec, int phase, int grid_cap, cu
     }
 }
 
+// The nine launches of a pair of steps n, n+1 (n even, depth 2), numbered
+// 0..8 (see the two-step pass): slab H, z-UPML, the pass, slab E, post (its
+// interior sources skipped), slab H with the band's H boxes, z-UPML, slab E
+// with the band's E boxes, post.  kPairPhase names the phase each belongs to.
+template <typename T>
+static cudaError_t pair_t(const Plan &plan, int idx, int grid_cap, cudaStream_t st)
+{
+    Plan p = plan;
+    switch (idx) {
+    case 2:
+        if (plan.n_pair > 0) {
+            cudaMemsetAsync(plan.work + 2, 0, sizeof(int), st);
+            PairCfg<T>::launch(plan, st);
+        }
+        return cudaGetLastError();
+    case 4: p.first_of_pair = 1; return phase_t<T>(p, kPhasePost, grid_cap, st);
+    case 5:   // the band's H+E blocks sit just before the slab blocks in the table
+        p.slab_blk -= plan.n_band_h;
+        p.n_slab += plan.n_band_h;
+        return phase_t<T>(p, kPhaseSlabH, grid_cap, st);
+    case 7:   // and its E-only blocks before those
+        p.slab_blk -= plan.n_band;
+        p.n_slab += plan.n_band;
+        return phase_t<T>(p, kPhaseSlabE, grid_cap, st);
+    default: return phase_t<T>(p, kPairPhase[idx], grid_cap, st);
+    }
+}
+
+cudaError_t launch_pair_part(const Plan &plan, int prec, int idx, int grid_cap, cudaStream_t st)
+{
+    switch (prec) {
+    case kFP16: return pair_t<__half>(plan, idx, grid_cap, st);
+    default: return pair_t<float>(plan, idx, grid_cap, st);
+    }
+}
+
+cudaError_t launch_pair(const Plan &plan, int prec, int grid_cap, cudaStream_t st)
+{
+    for (int i = 0; i < kPairLaunches; ++i) {
+        cudaError_t e = launch_pair_part(plan, prec, i, grid_cap, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_step(const Plan &plan, int prec, int grid_cap, cudaStream_t st)
 {
     for (int ph = 0; ph < kNumPhases; ++ph) {
@@ -1491,7 +2186,8 @@ bool fused_tile_supported(int tx, int ty) { return (tx == 62 || tx == 124) && (t
 template <typename T>
 static cudaError_t limits_t()
 {
-    cudaError_t e[10] = {cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
+    cudaError_t e[11] = {PairCfg<T>::set_limit(),
+                         cudaFuncSetAttribute(k_slab_h<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabHSmem),
                          cudaFuncSetAttribute(k_slab_e<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSlabESmem),
                          FusedCfg<T, 4, 1, false, 1>::set_limit(), FusedCfg<T, 8, 1, false, 4>::set_limit(),
                          FusedCfg<T, 4, 2, false, 1>::set_limit(), FusedCfg<T, 8, 2, false, 2>::set_limit(),

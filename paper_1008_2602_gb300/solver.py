@@ -107,8 +107,11 @@ class Solver:
         self._mat = np.ascontiguousarray(mat, dtype=np.uint8)
         C.fdtd_set_materials(self.ctx, self._mat.ctypes.data)
 
-    def set_tuning(self, tile_x=0, tile_y=0, zseg=0, graph_chunk=0):
-        t = C.fdtd_tuning(tile_x, tile_y, zseg, graph_chunk)
+    def set_tuning(self, tile_x=0, tile_y=0, zseg=0, graph_chunk=0, depth=0, pair_zseg=0):
+        """Kernel tuning (0 keeps a setting).  depth=2 advances the interior
+        region two leapfrog steps per pass (time blocking; bit-identical
+        results, one more field set in device memory)."""
+        t = C.fdtd_tuning(tile_x, tile_y, zseg, graph_chunk, depth, pair_zseg)
         C.fdtd_set_tuning(self.ctx, ctypes.byref(t))
 
     # -- results ---------------------------------------------------------------
@@ -198,8 +201,8 @@ class Batch:
         if tuning:
             self.set_tuning(**tuning)
 
-    def set_tuning(self, tile_x=0, tile_y=0, zseg=0, graph_chunk=0):
-        t = C.fdtd_tuning(tile_x, tile_y, zseg, graph_chunk)
+    def set_tuning(self, tile_x=0, tile_y=0, zseg=0, graph_chunk=0, depth=0, pair_zseg=0):
+        t = C.fdtd_tuning(tile_x, tile_y, zseg, graph_chunk, depth, pair_zseg)
         C.fdtd_batch_set_tuning(self.b, ctypes.byref(t))
 
     def add(self, s: Solver, n_steps: Optional[int] = None):
