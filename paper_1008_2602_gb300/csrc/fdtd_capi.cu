@@ -876,6 +876,17 @@ int build_plan(const std::vector<fdtd_ctx *> &boards, const fdtd_tuning &t, long
     plan.first_of_pair = 0;
     plan.n_band_h = band ? boards[0]->h.band_h_blocks : 0;
     plan.n_band = band ? boards[0]->h.band_blocks : 0;
+    plan.pc = PairConst{};
+    if (band) {
+        const Board &h = boards[0]->h;
+        PairConst &pc = plan.pc;
+        for (int a = 0; a < 3; ++a) pc.S[a] = h.S[a];
+        pc.ix0 = h.ix0; pc.ix1 = h.ix1; pc.iy0 = h.iy0; pc.iy1 = h.iy1; pc.iz0 = h.iz0; pc.iz1 = h.iz1;
+        pc.ny = h.ny; pc.pitch = h.pitch; pc.id16 = h.id16;
+        pc.plane = h.plane; pc.nodes = h.nodes;
+        pc.ctab = h.ctab;
+        pc.mid = h.f[2][0];
+    }
     return FDTD_OK;
 }
 

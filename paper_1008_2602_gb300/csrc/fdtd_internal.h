@@ -180,6 +180,18 @@ __host__ __device__ inline int set_of(int depth, long long n)
     return depth == 2 ? ((n & 1) ? 2 : (int)((n >> 1) & 1)) : (int)(n & 1);
 }
 
+// Constants of the single board a two-step pass works on, carried in the
+// plan (kernel parameters) so that the pass reads them from the constant
+// bank instead of holding them in registers.
+struct PairConst {
+    float S[3];
+    int ix0, ix1, iy0, iy1, iz0, iz1;
+    int ny, pitch, id16, pad;
+    long long plane, nodes;
+    const float4 *ctab;
+    void *mid;                    // component 0 of field set 2
+};
+
 // A launch plan over one or more boards: per-phase work-item prefix sums.
 struct Plan {
     int nb;
@@ -199,6 +211,7 @@ struct Plan {
     int first_of_pair;            // k_post: the step is the first of a two-step pass (its sources
                                   // inside I were applied by the pass)
     long long n_band_h, n_band;   // band blocks just before slab_blk[0] (E-only first, then H+E; second step of a pair)
+    PairConst pc;
 };
 
 // TMA descriptor slots of a board (3D maps: x, y, plane).

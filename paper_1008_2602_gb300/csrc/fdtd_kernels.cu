@@ -839,9 +839,10 @@ __device__ __forceinline__ PairTile decode_pair(const Plan &plan, long long item
     t.ok = active_ro(B) && B->pair_ok && B->tdepth == 2 && !(t.step & 1);
     t.in = set_of(2, t.step);
     t.out = set_of(2, t.step + 2);
-    const int ntx = (B->ix1 - B->ix0 + kPairCols - 1) / kPairCols;
-    const int nty = (B->iy1 - B->iy0 + kPairRows - 1) / kPairRows;
-    const int zs = plan.pair_zseg, iz0 = B->iz0, iz1 = B->iz1;
+    const PairConst &pc = plan.pc;
+    const int ntx = (pc.ix1 - pc.ix0 + kPairCols - 1) / kPairCols;
+    const int nty = (pc.iy1 - pc.iy0 + kPairRows - 1) / kPairRows;
+    const int zs = plan.pair_zseg, iz0 = pc.iz0, iz1 = pc.iz1;
     const int nseg = (iz1 - iz0 + zs - 1) / zs;
     const int wave_rows = max(1, plan.slots / ntx), nband = (nty + wave_rows - 1) / wave_rows;
     const int band = (nty + nband - 1) / nband;
@@ -852,8 +853,8 @@ __device__ __forceinline__ PairTile decode_pair(const Plan &plan, long long item
     const long long layer = (long long)ntx * rows;
     const int tz = (int)(within / layer);
     const int rem = (int)(within - tz * layer);
-    t.i0 = B->ix0 + (rem % ntx) * kPairCols;
-    t.j0 = B->iy0 + (bi * band + rem / ntx) * kPairRows;
+    t.i0 = pc.ix0 + (rem % ntx) * kPairCols;
+    t.j0 = pc.iy0 + (bi * band + rem / ntx) * kPairRows;
     t.kb = iz0 + tz * zs;
     t.ke = min(t.kb + zs, iz1);
     t.bot = t.kb == iz0;
@@ -981,17 +982,18 @@ __global__ void __launch_bounds__(PairLayout<T>::THREADS, 2) k_pair(Plan plan)
             const int i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke;
             const bool top = t.top;
             const int ps = t.bot ? kb : kb - 2, q0 = t.bot ? kb : kb - 1;
-            const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0, iz1 = B->iz1;
-            const int X = B->pitch, ny = B->ny;
-            const long long P = B->plane, NN = B->nodes;
-            const float2 Sx2 = make_float2(B->S[0], B->S[0]), Sy2 = make_float2(B->S[1], B->S[1]);
-            const float2 Sz2 = make_float2(B->S[2], B->S[2]);
-            const float2 nSx2 = make_float2(-B->S[0], -B->S[0]), nSy2 = make_float2(-B->S[1], -B->S[1]);
-            const float2 nSz2 = make_float2(-B->S[2], -B->S[2]);
-            const int id16 = B->id16;
-            const float4 *__restrict__ ctab = B->ctab;
-            int *const status = B->status;
-            T *const Mp = (T *)B->f[2][0];
+            const PairConst &pc = plan.pc;
+            const int ix0 = pc.ix0, ix1 = pc.ix1, iy0 = pc.iy0, iy1 = pc.iy1, iz0 = pc.iz0, iz1 = pc.iz1;
+            const int X = pc.pitch, ny = pc.ny;
+            const long long P = pc.plane, NN = pc.nodes;
+            const float2 Sx2 = make_float2(pc.S[0], pc.S[0]), Sy2 = make_float2(pc.S[1], pc.S[1]);
+            const float2 Sz2 = make_float2(pc.S[2], pc.S[2]);
+            const float2 nSx2 = make_float2(-pc.S[0], -pc.S[0]), nSy2 = make_float2(-pc.S[1], -pc.S[1]);
+            const float2 nSz2 = make_float2(-pc.S[2], -pc.S[2]);
+            const int id16 = pc.id16;
+            const float4 *__restrict__ ctab = pc.ctab;
+            int *const status = status0;
+            T *const Mp = (T *)pc.mid;
             const int g = i0 - 2;
             const int ca = g + 2 * lx, cb = ca + 1;
             const int whi = min(i0 + kPairCols, ix1);
@@ -1219,16 +1221,17 @@ __global__ void __launch_bounds__(PairLayout<T>::THREADS, 2) k_pair(Plan plan)
         const Board *__restrict__ B = t.B;
         const int i0 = t.i0, j0 = t.j0, kb = t.kb, ke = t.ke;
         const int q0 = t.bot ? kb : kb - 1;
-        const int ix0 = B->ix0, ix1 = B->ix1, iy0 = B->iy0, iy1 = B->iy1, iz0 = B->iz0;
-        const int X = B->pitch;
-        const long long P = B->plane, NN = B->nodes;
-        const float2 Sx2 = make_float2(B->S[0], B->S[0]), Sy2 = make_float2(B->S[1], B->S[1]);
-        const float2 Sz2 = make_float2(B->S[2], B->S[2]);
-        const float2 nSx2 = make_float2(-B->S[0], -B->S[0]), nSy2 = make_float2(-B->S[1], -B->S[1]);
-        const float2 nSz2 = make_float2(-B->S[2], -B->S[2]);
-        const int id16 = B->id16;
-        const float4 *__restrict__ ctab = B->ctab;
-        int *const status = B->status;
+        const PairConst &pc = plan.pc;
+        const int ix0 = pc.ix0, ix1 = pc.ix1, iy0 = pc.iy0, iy1 = pc.iy1, iz0 = pc.iz0;
+        const int X = pc.pitch;
+        const long long P = pc.plane, NN = pc.nodes;
+        const float2 Sx2 = make_float2(pc.S[0], pc.S[0]), Sy2 = make_float2(pc.S[1], pc.S[1]);
+        const float2 Sz2 = make_float2(pc.S[2], pc.S[2]);
+        const float2 nSx2 = make_float2(-pc.S[0], -pc.S[0]), nSy2 = make_float2(-pc.S[1], -pc.S[1]);
+        const float2 nSz2 = make_float2(-pc.S[2], -pc.S[2]);
+        const int id16 = pc.id16;
+        const float4 *__restrict__ ctab = pc.ctab;
+        int *const status = status0;
         const int g = i0 - 2;
         const int ca = g + 2 * lx, cb = ca + 1;
         const int whi = min(i0 + kPairCols, ix1);
