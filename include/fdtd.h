@@ -284,14 +284,15 @@ int fdtd_node_coefficients(const fdtd_grid *grid, const uint8_t *mat_ids, const 
 
 /* Host only: the device memory [bytes] a board needs, without touching a
  * device: what fdtd_create allocates for the grid and boundary (fields of
- * both parities in the given precision, per-node coefficient ids counted at
+ * two field sets in the given precision, per-node coefficient ids counted at
  * 16 bits with a 65536-row table, the 1D UPML factors, the auxiliaries of the
  * UPML boxes as fdtd_create lays them out, counters and scratch), plus what
  * the first step adds: the tensor maps, n_sources sources, n_probes probes
  * with traces of n_total_steps samples and the running DFT's bins up to f_max
  * (as in fdtd_set_spectrum).  An upper bound on fdtd_info's device_bytes by at
  * most one byte per node and the table's 1 MB (8-bit ids when at most 256
- * edge coefficient triples occur).  Serves admission by memory budget.
+ * edge coefficient triples occur), at depth 1 (fdtd_tuning: depth 2 adds a
+ * third field set).  Serves admission by memory budget.
  * Errors: FDTD_EINVAL for the cases fdtd_create refuses on grid, boundary or
  * precision. */
 int fdtd_device_bytes(const fdtd_grid *grid, const fdtd_boundary *bnd, int precision, int n_sources, int n_probes,
