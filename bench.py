@@ -242,7 +242,7 @@ def run_single(args, world, rank, local):
     step_bytes = bytes_per_node * (interior_nodes + inf["slab_nodes"]) + 16 * upml_nodes + 8 * inf["slab_aux_values"]
     t_leap = elapsed / (window * args.steps)
     peak, peak_kind = _measured_peaks()
-    traffic = _traffic_for(f"k_fused_interior_{args.precision}", int_nodes)
+    traffic = _traffic_for(f"{'k_fused_interior' if depth == 1 else 'k_pair'}_{args.precision}", int_nodes)
 
     # e2e: host buffers through the C-ABI
     e2e = None

@@ -229,3 +229,40 @@ def test_tuner_searches_the_blocking_depth(fdtd, tmp_path, monkeypatch):
     assert np.array_equal(t_tuned, t_ref)
     cfg2 = tune.tune([p, p], steps=4, shapes=[(62, 8)], zsegs=[10], chunks=[16])
     assert cfg2["depth"] == 1
+
+
+def test_depth2_boards_in_a_batch_and_a_split(fdtd):
+    """A depth-2 board stepped inside a batch runs single steps in the depth-2
+    set order, and a board split along y whose parts are depth-2 contexts
+    steps one step at a time with halo copies between the parts' current
+    sets.  Both give the same bits as the boards alone at depth 1."""
+    from paper_1008_2602_gb300 import decomp
+    p = band_problem(11, (150, 44, 30), 4, "fp32", 77)
+    q = band_problem(12, (97, 30, 19), 0, "fp32", 50)
+    alone = []
+    for prob in (p, q):
+        f, t, _, _, _ = _run(fdtd, prob, "fp32", prob.n_steps)
+        alone.append((f, t))
+    b = fdtd.Batch()
+    sol = [fdtd.Solver(p, tuning=dict(depth=2)), fdtd.Solver(q)]
+    assert sol[0].info()["depth"] == 2
+    sol[0].step(3)   # an odd step count on its own before joining
+    b.add(sol[0], p.n_steps - 3)
+    b.add(sol[1])
+    done = 0
+    while done < 2:
+        done = b.step(16)
+    b.sync()
+    for s, (f, t) in zip(sol, alone):
+        for c in range(6):
+            assert np.array_equal(s.field(c), f[c]), c
+        assert np.array_equal(s.traces(), t)
+    b.close()
+    for s in sol:
+        s.close()
+    sp = decomp.SplitSolver(p, [21], tuning=dict(depth=2))
+    sp.step(p.n_steps)
+    for c in range(6):
+        assert np.array_equal(sp.field(c), alone[0][0][c]), c
+    assert np.array_equal(sp.traces(), alone[0][1])
+    sp.close()
