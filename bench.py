@@ -46,6 +46,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Yee+UPML Gcell-updates/s & % HBM roofline; batched/served solves/s, p50/p99 latency"
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 
 
 def _measured_peaks():
@@ -283,6 +284,7 @@ def run_single(args, world, rank, local):
                      if depth == 1 else "k_pair two-step interior pass (two leapfrog steps per launch; the phase "
                      "also holds the window's single-step interior launches)",
                      "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
                      "traffic": traffic, "peak_source": peak_kind,
                      "bytes_per_unit": bytes_per_node, "units_per_launch": int_nodes,
                      "algorithmic_bytes_per_launch": alg_bytes, "mean_launch_ms": round(t_int * 1e3, 5)},
@@ -291,17 +293,20 @@ def run_single(args, world, rank, local):
                           "bytes_per_cell": round(step_bytes / cells, 2),
                           "achieved": round(step_bytes / t_leap / 1e9, 1), "peak": peak, "unit": "GB/s",
                           "frac": round(step_bytes / t_leap / 1e9 / peak, 4),
+                          "frac_of_nominal": round(step_bytes / t_leap / 1e9 / NOMINAL_HBM_GBS, 4),
                           "roofline_gcell_updates_per_s": round(cells / (step_bytes / (peak * 1e9)) / 1e9, 2)},
         "roofline_zupml": {"kernel": "k_fused z-UPML launch", "bytes_per_unit": bytes_per_node + 16,
                            "units_per_launch": upml_nodes, "mean_launch_ms": round(t_zp * 1e3, 5),
                            "achieved": round(zp_bytes / t_zp / 1e9, 1) if t_zp > 0 else None,
-                           "frac": round(zp_bytes / t_zp / 1e9 / peak, 4) if t_zp > 0 else None},
+                           "frac": round(zp_bytes / t_zp / 1e9 / peak, 4) if t_zp > 0 else None,
+                           "frac_of_nominal": round(zp_bytes / t_zp / 1e9 / NOMINAL_HBM_GBS, 4) if t_zp > 0 else None},
         "roofline_slab": {"kernel": "k_slab_h + k_slab_e (UPML faces, edges, corners, z-UPML rings, wall planes)",
                           "bytes_per_unit": bytes_per_node, "aux_bytes_per_value": 8,
                           "units_per_launch": int(inf["slab_nodes"]), "aux_values": int(inf["slab_aux_values"]),
                           "mean_launch_ms": round(t_sl * 1e3, 5),
                           "achieved": round(sl_bytes / t_sl / 1e9, 1) if t_sl > 0 else None,
-                          "frac": round(sl_bytes / t_sl / 1e9 / peak, 4) if t_sl > 0 else None},
+                          "frac": round(sl_bytes / t_sl / 1e9 / peak, 4) if t_sl > 0 else None,
+                          "frac_of_nominal": round(sl_bytes / t_sl / 1e9 / NOMINAL_HBM_GBS, 4) if t_sl > 0 else None},
         "tuning": {"tile_x": args.tile_x or "default", "tile_y": args.tile_y or "default",
                    "zseg": args.zseg or "default", "depth": depth, "pair_zseg": args.pair_zseg or "default"},
         "gpu_launches": int(args.steps * (singles * (5 if upml_nodes else 4) + pairs * (9 if upml_nodes else 7) + 2)),
