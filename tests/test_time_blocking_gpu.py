@@ -266,3 +266,21 @@ def test_depth2_boards_in_a_batch_and_a_split(fdtd):
         assert np.array_equal(sp.field(c), alone[0][0][c]), c
     assert np.array_equal(sp.traces(), alone[0][1])
     sp.close()
+
+
+def test_depth2_fp16_long_run_meets_the_storage_bar(fdtd, ncpu):
+    """FP16 storage at depth 2 over the small PCB's 2000 steps: every probe
+    trace within 1e-2 (relative L2) of the FP64 oracle and the spectral peaks
+    in the oracle's bins, as for depth 1."""
+    p = W.small_pcb()
+    ref = oracle.run(p, n_threads=ncpu)
+    s = fdtd.Solver(p, precision="fp16", tuning=dict(depth=2))
+    assert s.info()["depth"] == 2
+    s.run()
+    tr = s.traces()
+    errs = [rel_l2(tr[q], ref["trace"][q]) for q in range(len(tr))]
+    assert max(errs) <= 1e-2, errs
+    sp = s.spectra()
+    for q in range(len(tr)):
+        assert np.argmax(np.abs(sp[q][1:])) == np.argmax(np.abs(ref["spectra"][q][1:]))
+    s.close()
