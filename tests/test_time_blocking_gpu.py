@@ -60,19 +60,25 @@ def interior(p, prec="fp32"):
     return ix0, ix1, max(d[2], 1), p.ny - d[3], max(d[4], 1), p.nz - d[5]
 
 
-def band_problem(seed, shape, upml, prec, n_steps):
+def band_problem(seed, shape, upml, prec, n_steps, **over):
     """A random problem plus sources and probes on the band and inside I.
 
     The band is the one-node outer layer of I.  The extra sources are E_z
     edges, which a PEC sheet never covers, plus an E_x and an E_y edge off
     the sheet's plane.  One resistive voltage source sits inside I and one
-    on a band corner."""
+    on a band corner.  `over` replaces problem fields (UPML depths, walls,
+    kappa_max) first; the random sources that then fall in a UPML are
+    dropped."""
     p = W.random_problem(seed, *shape, upml=upml, n_steps=n_steps)
+    if over:
+        p = p.replace(**over)
+    d, n = p.upml_depth, (p.nx, p.ny, p.nz)
     ix0, ix1, iy0, iy1, iz0, iz1 = interior(p, prec)
     kk = int(np.asarray(p.pec_boxes).reshape(-1, 6)[0][4])
     jm, km = (iy0 + iy1) // 2, (iz0 + iz1) // 2
     kx = km if km != kk else km + 1
-    src = [tuple(int(v) for v in s) for s in np.asarray(p.sources).reshape(-1, 4)]
+    src = [tuple(int(v) for v in s) for s in np.asarray(p.sources).reshape(-1, 4)
+           if all(d[2 * a] <= s[a] <= n[a] - d[2 * a + 1] - 1 for a in range(3))]
     src += [(ix0, jm, km, 2), (ix1 - 1, jm + 1, km, 2), (ix0 + 5, iy0, iz0, 2), (ix0 + 7, iy1 - 1, iz1 - 1, 2),
             (ix0 + 3, jm, iz0, 2), (ix0 + 2, jm, kx, 0), (ix1 - 2, jm - 1, kx, 1), (ix0 + 2, jm, kx, 0)]
     prb = [tuple(int(v) for v in q) for q in np.asarray(p.probes).reshape(-1, 4)]
@@ -173,6 +179,26 @@ def test_depth_switch_checkpoint_and_diagnostics(fdtd):
         assert np.array_equal(a.field(c), ref.field(c)), c
     a.close()
     ref.close()
+
+
+@pytest.mark.parametrize("variant", ["kappa5", "pmc_sides"])
+def test_depth2_bitwise_with_stretched_upml_and_pmc_walls(fdtd, variant):
+    """Depth 2 runs the slab and z-UPML launches of both steps through the
+    three field sets; their auxiliaries keep the step parity.  Checked
+    bitwise against depth 1 with kappa_max = 5 (m = 3) in an uneven UPML, and
+    on a board with PMC x and y walls and no x/y UPML (z-UPML only)."""
+    if variant == "kappa5":
+        p = band_problem(13, (140, 41, 28), 4, "fp32", 45, upml_kappa_max=5.0, upml_depth=(4, 6, 5, 4, 4, 6))
+    else:
+        p = band_problem(14, (120, 37, 26), 4, "fp32", 45, upml_depth=(0, 0, 0, 0, 4, 4),
+                         walls=(W.WALL_PMC,) * 4 + (W.WALL_PEC,) * 2)
+    f1, t1, _, _, g1 = _run(fdtd, p, "fp32", 45)
+    f2, t2, _, d2, g2 = _run(fdtd, p, "fp32", 45, depth=2, pair_zseg=6)
+    assert d2 == 2
+    for c in range(6):
+        assert np.array_equal(f1[c], f2[c]), c
+    assert np.array_equal(t1, t2)
+    assert g1 == g2
 
 
 def test_depth2_falls_back_where_the_pass_cannot_run(fdtd):
