@@ -392,18 +392,46 @@ struct IdScratch {
     std::unique_ptr<uint16_t[]> cid;
     std::unique_ptr<uint8_t[]> c8;
     size_t cap = 0;
+    bool pinned = false;          // registered with CUDA (page-locked) for the uploads
     void reserve(size_t n)
     {
         if (n <= cap) return;
+        unpin();
         cid.reset(new uint16_t[n]);
         c8.reset(new uint8_t[n]);
         cap = n;
     }
+    // Page-lock the buffers once, so that uploads of the ids are asynchronous
+    // DMA copies from pinned memory (host-only callers never need it; if the
+    // registration fails the copies still work from pageable memory).
+    void pin()
+    {
+        if (pinned || !cap) return;
+        const bool a = cudaHostRegister(cid.get(), cap * sizeof(uint16_t), cudaHostRegisterDefault) == cudaSuccess;
+        const bool b = cudaHostRegister(c8.get(), cap, cudaHostRegisterDefault) == cudaSuccess;
+        if (!(a && b)) {
+            if (a) cudaHostUnregister(cid.get());
+            if (b) cudaHostUnregister(c8.get());
+            cudaGetLastError();
+            return;
+        }
+        pinned = true;
+    }
+    void unpin()
+    {
+        if (!pinned) return;
+        cudaHostUnregister(cid.get());
+        cudaHostUnregister(c8.get());
+        cudaGetLastError();
+        pinned = false;
+    }
 };
+// Never destroyed: its buffers may be page-locked, and the CUDA runtime may
+// already be shut down when static destructors run.
 IdScratch &id_scratch()
 {
-    static IdScratch s;
-    return s;
+    static IdScratch *s = new IdScratch;
+    return *s;
 }
 
 int build_combo(const fdtd_ctx *c, const uint8_t *mat, NodeIds &ids, std::vector<float4> &table)
@@ -1043,6 +1071,7 @@ int set_geometry(fdtd_ctx *c, const uint8_t *mat)
     } catch (const std::bad_alloc &) {
         return fail(FDTD_ENOMEM, "host scratch for the coefficient ids");
     }
+    scratch.pin();
     ids.cid = scratch.cid.get();
     ids.c8 = scratch.c8.get();
     std::vector<float4> table;
