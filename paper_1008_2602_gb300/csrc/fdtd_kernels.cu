@@ -13,8 +13,11 @@
 //                   (Results section) and probe samples of E^{n+1}
 // and, once per chunk, k_dft folds the new probe samples into the FP64
 // running DFT (Results section: spectrum of the ground-plane E_z) with warp
-// shuffles.  Fields are ping-ponged, so no launch reads what it writes except
-// the per-node UPML auxiliaries, which only their own thread touches.
+// shuffles.  Each step reads one field set and writes another (set_of), so no
+// launch reads what it writes except the per-node UPML auxiliaries, which
+// only their own thread touches.  With time blocking (depth 2) a pair of
+// steps replaces the two interior launches by one two-step pass (k_pair) and
+// lets the slab kernels finish the interior region's outer layer.
 //
 // All curl and update arithmetic goes through curl2()/the update helpers (or
 // their paired FFMA2 forms) with explicit round-to-nearest intrinsics, so a
