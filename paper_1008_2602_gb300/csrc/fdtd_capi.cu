@@ -968,15 +968,11 @@ int run_depth2(const Plan &plan, int prec, int grid_cap, long long step, int n, 
 {
     if (n <= 0) return FDTD_OK;
     NvtxRange range("fdtd step pairs");
-    int left = n;
-    bool direct = false;
-    if (step & 1) {
-        CK(launch_step(plan, prec, grid_cap, st));
-        --left;
-        direct = true;
-    }
-    int pairs = left >= 3 ? (left - 1) / 2 : 0;
-    left -= 2 * pairs;
+    const PairSplit sp = pair_split(step, n);
+    if (sp.lead) CK(launch_step(plan, prec, grid_cap, st));
+    const bool direct = sp.lead != 0;
+    int pairs = sp.pairs;
+    const int left = sp.tail;
     const int cp = std::max(1, chunk / 2);
     if (cp > 1 && pairs >= cp) {
         if (!graph2 || graph2_chunk != cp) {
@@ -1030,15 +1026,11 @@ int set_time_depth(fdtd_ctx *c, int d)
     CK(cudaStreamSynchronize(c->cur));
     if (d != old) {
         const long long n = c->host_step;
-        const int a = set_of(old, n), b = set_of(old, n - 1), x = set_of(d, n), y = set_of(d, n - 1);
+        int perm[3];
+        rename_sets(old, d, n, perm);
         void *f[3][6];
-        bool used[3] = {false, false, false};
-        for (int q = 0; q < 6; ++q) { f[x][q] = h.f[a][q]; f[y][q] = h.f[b][q]; }
-        used[a] = used[b] = true;
-        int spare = 0;
-        while (spare < 3 && used[spare]) ++spare;
-        const int z = 3 - x - y;
-        for (int q = 0; q < 6; ++q) f[z][q] = spare < 3 ? h.f[spare][q] : nullptr;
+        for (int x = 0; x < 3; ++x)
+            for (int q = 0; q < 6; ++q) f[x][q] = h.f[perm[x]][q];
         std::memcpy(h.f, f, sizeof(f));
         h.tdepth = d;
         h.tm_tx = 0;   // the tensor maps name the sets' addresses
@@ -1477,14 +1469,13 @@ int fdtd_step_profiled(fdtd_ctx *c, int n, double *phase_ms)
     // the launch sequence: single steps (five launches) and, with depth 2,
     // pairs (nine launches); the same split as fdtd_step
     std::vector<int> unit;   // 1: single step, 2: pair
-    {
-        long long s = c->host_step;
-        int left = n;
-        if (c->h.pair_ok && (s & 1) && left > 0) { unit.push_back(1); --left; }
-        int pairs = c->h.pair_ok && left >= 3 ? (left - 1) / 2 : 0;
-        for (int p = 0; p < pairs; ++p) unit.push_back(2);
-        left -= 2 * pairs;
-        for (int q = 0; q < left; ++q) unit.push_back(1);
+    if (c->h.pair_ok) {
+        const PairSplit sp = pair_split(c->host_step, n);
+        unit.assign(sp.lead, 1);
+        unit.insert(unit.end(), sp.pairs, 2);
+        unit.insert(unit.end(), sp.tail, 1);
+    } else {
+        unit.assign(n, 1);
     }
     std::vector<int> phase_of;   // phase of each timed launch
     size_t ev = 0;

@@ -192,6 +192,41 @@ struct PairConst {
     void *mid;                    // component 0 of field set 2
 };
 
+// How a depth-2 board runs n steps from step s: one single step to reach an
+// even step, then pairs (one two-step pass each), then one or two single
+// steps, so that the last step is a single one and the states after the
+// last two steps are complete in memory.
+struct PairSplit {
+    int lead, pairs, tail;
+};
+inline PairSplit pair_split(long long s, int n)
+{
+    PairSplit p{0, 0, 0};
+    if (n <= 0) return p;
+    int left = n;
+    if (s & 1) {
+        p.lead = 1;
+        --left;
+    }
+    p.pairs = left >= 3 ? (left - 1) / 2 : 0;
+    p.tail = left - 2 * p.pairs;
+    return p;
+}
+
+// Renaming of the field sets when the blocking depth changes from d0 to d1
+// after n steps: the new set x is the old set perm[x], so that the states
+// after steps n and n - 1 sit where set_of(d1, .) expects them (the third set
+// takes the spare one).
+inline void rename_sets(int d0, int d1, long long n, int perm[3])
+{
+    const int a = set_of(d0, n), b = set_of(d0, n - 1), x = set_of(d1, n), y = set_of(d1, n - 1);
+    int spare = 0;
+    while (spare == a || spare == b) ++spare;
+    perm[x] = a;
+    perm[y] = b;
+    perm[3 - x - y] = spare;
+}
+
 // A launch plan over one or more boards: per-phase work-item prefix sums.
 struct Plan {
     int nb;
